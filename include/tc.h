@@ -1,0 +1,218 @@
+/*
+ * tc.h -- exact triangle counting on one GB300 GPU (sm_103a), after TRUST
+ * (Pandey, Wang et al., "TRUST: Triangle Counting Reloaded on GPUs").
+ *
+ * The library counts the triangles (three-vertex cliques, Sec. 1) of a
+ * simple undirected graph given as a symmetric CSR (Sec. 2.1: "begin
+ * position" = row_ptr, "adjacency list" = col). The hot path is the paper's
+ * vertex-centric hashing method (Sec. 3, Algorithm 1):
+ *   1. rank-by-degree orientation (Sec. 2.2) turns the undirected CSR into a
+ *      DAG N+ in which every edge points from the lower to the higher
+ *      (degree, id) pair, so every triangle is seen exactly once;
+ *   2. vertices are binned by out-degree d+ (Sec. 4.3): d+ < 2 is skipped,
+ *      small vertices go to warp workers, large ones to thread-block workers;
+ *   3. for every vertex u a bucketed hash table of N+(u) is built once in
+ *      shared memory (Algorithm 1 hashTableConstruction, Sec. 3.1-3.2:
+ *      fixed-size buckets, atomic slot counters, level-major layout, overflow
+ *      to the next bucket), then probed with N+(v) for every v in N+(u)
+ *      (Algorithm 1 intersection / linearSearch), with the 2-hop lists of all
+ *      v spread evenly over the lanes by virtual combination (Sec. 4.2);
+ *   4. hits are summed into one 64-bit count.
+ * Everything runs in the library's own CUDA kernels; there is no CPU path.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a tc_status; none aborts, prints or throws. On any
+ *     status other than TC_OK the output arguments are left untouched and
+ *     tc_last_error(ctx) describes the failure.
+ *   - "device" pointers are CUDA device (or managed) memory of the context's
+ *     device; "host" pointers are ordinary (pageable or pinned) host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream). Device inputs must stay valid and unmodified until the call
+ *     returns (blocking calls) or until the stream reaches the call's work
+ *     (the *_async calls).
+ *   - A context is not thread-safe, except tc_submit / tc_poll / tc_cancel,
+ *     which may be called from any thread at any time.
+ *
+ * Input preconditions (not all checked): the CSR is symmetric (v in N(u) iff
+ * u in N(v)) with no duplicate entries in a row; rows need not be sorted;
+ * self-loops are allowed and ignored (the strict order drops u -> u). Column
+ * ids outside [0, n) are always detected and reported as TC_ERR_BAD_GRAPH.
+ * With tc_params.validate = 1 the library also checks row_ptr monotonicity
+ * and symmetry-implied sizes before counting.
+ */
+#ifndef TRUST_GB300_TC_H
+#define TRUST_GB300_TC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TC_OK = 0,
+    TC_ERR_INVALID_ARG = 1, /* NULL pointer, negative size, bad enum value */
+    TC_ERR_BAD_GRAPH = 2,   /* malformed CSR detected (column out of range, ...) */
+    TC_ERR_OOM = 3,         /* device allocation failed or memory budget exceeded */
+    TC_ERR_BUSY = 4,        /* serving queue full / request exceeds the budget */
+    TC_ERR_NOT_READY = 5,   /* tc_poll: the request has not finished yet */
+    TC_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+    TC_ERR_CUDA = 7,        /* a CUDA runtime call failed (see tc_last_error) */
+    TC_ERR_UNSUPPORTED = 8  /* valid input outside the supported range */
+} tc_status;
+
+typedef struct tc_ctx tc_ctx;
+
+/* A simple undirected graph as a symmetric CSR (Sec. 2.1).
+ * row_ptr: n+1 offsets, int32 when offset_bits == 32, int64 when 64;
+ *          row_ptr[0] == 0, non-decreasing, row_ptr[n] == nnz.
+ * col:     nnz int32 neighbour ids; N(u) = col[row_ptr[u] .. row_ptr[u+1]).
+ * Each undirected edge {u,v} appears twice (in N(u) and in N(v)), so nnz is
+ * 2|E|. Whether the pointers are host or device memory depends on the call. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const void* row_ptr;
+    int32_t offset_bits;
+    const int32_t* col;
+} tc_csr;
+
+/* The oriented graph N+ (Sec. 2.2 rank-by-degree; Sec. 4.3 "after
+ * orientation"): dag_ptr int32[n+1], dag_col int32[m], device memory. m is the
+ * number of undirected edges (each kept once); m must be < 2^31. A tc_dag
+ * filled by tc_orient is owned by the context and released by tc_dag_free;
+ * a caller may also fill one with its own device buffers for tc_count_dag. */
+typedef struct {
+    int64_t n;
+    int64_t m;
+    int32_t* dag_ptr;
+    int32_t* dag_col;
+} tc_dag;
+
+/* Tunables. Zero in any field means "use the default" (tc_default_params).
+ * The paper's constants are noted beside each (Sec. 3.1, 3.2, 4.3). */
+typedef struct {
+    int32_t warp_max_out_degree; /* d+ above this -> thread-block worker (paper: 100; default 128) */
+    int32_t warp_table_ints;     /* per-warp hash table capacity, ints (paper: 32 buckets x 6 levels in smem) */
+    int32_t warp_max_buckets;    /* bucket count cap for warp tables (power of two; paper: 32) */
+    int32_t max_levels;          /* maximum collision count L of a bucket before overflow (paper: 128) */
+    int32_t block_threads;       /* threads of a thread-block worker (default 1024) */
+    int32_t block_smem_bytes;    /* shared memory of a thread-block worker (default 200 KiB) */
+    int32_t item_neighbors;      /* out-neighbours of a large vertex per work item (default 1024) */
+    int32_t chunk;               /* vertices a warp takes per queue pop (Sec. 4.3; paper: 1..7) */
+    int32_t warps_per_block;     /* warps per block of the warp-worker kernel (default 8) */
+    int32_t shard_count;         /* workload partition (Sec. 5.1): count only u with */
+    int32_t shard_index;         /*   u % shard_count == shard_index (default 1 / 0) */
+    int32_t validate;            /* 1: check row_ptr monotonicity on the device first */
+    int32_t reserved[4];
+} tc_params;
+
+/* Per-DAG statistics (tc_dag_stats), all exact:
+ * wedges_plus = W+ = sum_u sum_{v in N+(u)} d+(v), the number of hash probes
+ * (the oriented "collective degree" of Eq. 2 summed over u). */
+typedef struct {
+    int64_t n, m;
+    int64_t max_out_degree;
+    int64_t n_skip;        /* d+ < 2 */
+    int64_t n_warp;        /* 2 <= d+ <= warp_max_out_degree */
+    int64_t n_block;       /* d+ > warp_max_out_degree */
+    int64_t wedges_plus;   /* W+ */
+    int64_t wedges_plus_block; /* part of W+ owned by thread-block vertices */
+} tc_stats;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Fill *p with the defaults. */
+tc_status tc_default_params(tc_params* p);
+
+/* Create a context on CUDA device `device`. mem_budget_bytes caps the device
+ * memory the context may hold for serving (0 = no cap). p may be NULL
+ * (defaults). The context owns a grow-only device workspace. */
+tc_status tc_create(tc_ctx** ctx, int device, size_t mem_budget_bytes, const tc_params* p);
+
+/* Wait for the context's work, free everything it owns. ctx may be NULL. */
+tc_status tc_destroy(tc_ctx* ctx);
+
+tc_status tc_set_params(tc_ctx* ctx, const tc_params* p);
+tc_status tc_get_params(tc_ctx* ctx, tc_params* p);
+
+/* ---- the hot path --------------------------------------------------------- */
+
+/* Rank-by-degree orientation (Sec. 2.2): keep u -> v iff
+ * (deg u, u) < (deg v, v) lexicographically, where deg is the undirected
+ * degree. g: device CSR. On TC_OK, *out holds context-owned device arrays with
+ * the kept neighbours of every row in input order; release with tc_dag_free.
+ * Blocks until m is known on the host. */
+tc_status tc_orient(tc_ctx* ctx, const tc_csr* g, tc_dag* out, void* stream);
+tc_status tc_dag_free(tc_ctx* ctx, tc_dag* dag);
+
+/* Count the triangles of an oriented graph (Algorithm 1 on N+; Sec. 4.2-4.3).
+ * dag: device arrays (rows in any order, no duplicates). count_host: the
+ * total. per_vertex_device: NULL, or device uint64[n] that receives, for
+ * every u, the triangles whose lowest vertex in the orientation order is u
+ * (sum_{v in N+(u)} |N+(u) ∩ N+(v)|). Blocks until the count is on the host. */
+tc_status tc_count_dag(tc_ctx* ctx, const tc_dag* dag, uint64_t* count_host, uint64_t* per_vertex_device,
+                       void* stream);
+
+/* Orient + count (the whole path). g: device CSR. Blocks; *count_host = T(G). */
+tc_status tc_count(tc_ctx* ctx, const tc_csr* g, uint64_t* count_host, void* stream);
+
+/* Same work as tc_count, fully asynchronous: the count (uint64) is written to
+ * count_device when the stream reaches it, no host synchronisation happens,
+ * and a malformed graph sets *error_device (int32, device; may be NULL) to a
+ * nonzero tc_status instead of returning it. Capturable in a CUDA graph once
+ * the context's workspace is large enough for g (call tc_reserve first). */
+tc_status tc_count_async(tc_ctx* ctx, const tc_csr* g, uint64_t* count_device, int32_t* error_device,
+                         void* stream);
+
+/* Grow the workspace for graphs up to n vertices and nnz entries, so that
+ * later calls on such graphs allocate nothing. */
+tc_status tc_reserve(tc_ctx* ctx, int64_t n, int64_t nnz);
+
+/* The whole path from host memory: copies the host CSR g to the device,
+ * orients, counts, and copies the count back. Blocks. */
+tc_status tc_count_host(tc_ctx* ctx, const tc_csr* g, uint64_t* count_host, void* stream);
+
+/* Exact statistics of an oriented graph (out-degree bins, W+). Blocks. */
+tc_status tc_dag_stats(tc_ctx* ctx, const tc_dag* dag, tc_stats* out, void* stream);
+
+/* ---- batched counting ----------------------------------------------------- */
+
+/* Count k independent graphs in one pass: all graphs are oriented by one
+ * launch sequence and counted by one persistent kernel whose work items are
+ * (graph, vertex) pairs. gs: k device CSRs (int32 or int64 offsets).
+ * counts_host: k results. Blocks. */
+tc_status tc_count_batch(tc_ctx* ctx, const tc_csr* gs, int32_t k, uint64_t* counts_host, void* stream);
+
+/* ---- serving -------------------------------------------------------------- */
+
+/* Queue a counting request. g: HOST CSR; the library copies it into its own
+ * device memory before the request runs (the caller may free g once
+ * tc_submit returns). Requests are admitted as device memory within the
+ * context's budget frees up and run concurrently with the requests already on
+ * the GPU (continuous batching). *ticket identifies the request.
+ * TC_ERR_BUSY: the request alone exceeds the budget. */
+tc_status tc_submit(tc_ctx* ctx, const tc_csr* g, uint64_t* ticket);
+
+/* TC_OK and *count once request `ticket` finished (the ticket is then
+ * retired); TC_ERR_NOT_READY while it is queued or running; the request's own
+ * error status if it failed; TC_ERR_INVALID_ARG for an unknown ticket. */
+tc_status tc_poll(tc_ctx* ctx, uint64_t ticket, uint64_t* count);
+
+/* Block until every submitted request has finished. */
+tc_status tc_drain(tc_ctx* ctx);
+
+/* ---- diagnostics ---------------------------------------------------------- */
+
+const char* tc_status_string(tc_status s);
+/* Text of the last failure on ctx (empty if none). Valid until the next call. */
+const char* tc_last_error(tc_ctx* ctx);
+/* Library version string. */
+const char* tc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRUST_GB300_TC_H */

@@ -1,0 +1,90 @@
+// api_internal.h -- host-side state of a tc_ctx (not installed).
+#pragma once
+
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "tc_internal.h"
+
+namespace tcg {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    // Grow-only: (re)allocates when `need` exceeds the current size, after
+    // synchronising `st` so no queued kernel still reads the old buffer.
+    tc_status ensure(tc_ctx* ctx, size_t need, cudaStream_t st);
+    void release(tc_ctx* ctx);
+};
+
+// Scratch of one counting pass.
+struct Workspace {
+    DevBuf deg, kept, partial, dag_ptr, dag_col, warp_list, items, ctr, stats;
+    void release_all(tc_ctx* ctx) {
+        for (DevBuf* b : {&deg, &kept, &partial, &dag_ptr, &dag_col, &warp_list, &items, &ctr, &stats})
+            b->release(ctx);
+    }
+};
+
+struct BufPair {
+    DevBuf a, b;
+    void release_all(tc_ctx* ctx) {
+        a.release(ctx);
+        b.release(ctx);
+    }
+};
+
+class DeviceGuard {
+   public:
+    explicit DeviceGuard(int dev);
+    ~DeviceGuard();
+
+   private:
+    int prev_ = -1, dev_ = -1;
+};
+
+struct BatchState;  // batch.cu
+struct ServeState;  // serve.cu
+
+}  // namespace tcg
+
+struct tc_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int max_smem_optin = 0;
+    size_t mem_budget = 0;
+    std::atomic<long long> held_bytes{0};
+    tc_params params{};
+    tcg::CountCfg cfg{};
+    char last_error[512] = {0};
+    tcg::Workspace ws;
+    tcg::DevBuf out_scalars;          // device: count (8 B) + error (4 B)
+    tcg::BufPair csr_copy;            // device copy of a host CSR (tc_count_host)
+    tcg::DevCounters* host_ctr = nullptr;  // pinned
+    std::map<void*, void*> dags;      // tc_orient allocations: dag_ptr -> dag_col
+    tcg::BatchState* batch = nullptr;
+    tcg::ServeState* serve = nullptr;
+};
+
+namespace tcg {
+
+tc_status ctx_fail(tc_ctx* ctx, tc_status s, const char* fmt, ...);
+tc_status cuda_status(tc_ctx* ctx, cudaError_t e, const char* what);
+tc_status err_bits_status(int bits);
+const char* err_bits_text(int bits);
+tc_status resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, CountCfg* cfg);
+tc_status check_csr(tc_ctx* ctx, const tc_csr* g);
+tc_status ensure_count_ws(tc_ctx* ctx, Workspace& ws, int64_t n, int64_t m, cudaStream_t st);
+tc_status ensure_orient_ws(tc_ctx* ctx, Workspace& ws, int64_t n, int64_t nnz, cudaStream_t st);
+
+void batch_release(tc_ctx* ctx);  // batch.cu
+void serve_shutdown(tc_ctx* ctx); // serve.cu
+
+}  // namespace tcg

@@ -1,0 +1,310 @@
+// orient.cu -- rank-by-degree orientation and out-degree binning.
+//
+// Orientation (TRUST Sec. 2.2, rank-by-degree; Sec. 4.3 "after orientation"):
+// an undirected edge {u,v} is kept once, as u -> v, iff
+// (deg u, u) < (deg v, v) lexicographically, deg being the undirected
+// degree. Every triangle then has exactly one vertex with both other vertices
+// in its out-list, so Algorithm 1 run on N+ counts each triangle once.
+//
+// Kernels, in launch order (all HBM-streaming):
+//   k_degree        deg[u] = row_ptr[u+1] - row_ptr[u]          (reads 8|4 B/row)
+//   k_orient<count> kept[u] = #{v in N(u) : rank u < rank v}    (reads col + deg gather)
+//   k_scan_*        dag_ptr = exclusive scan of kept (int64 carry, int32 out)
+//   k_orient<compact> dag_col = kept neighbours, input order   (re-reads col, writes m)
+// A warp owns 32 consecutive rows and walks their concatenated neighbour
+// lists with coalesced 32-lane loads; each lane finds its row by a forward
+// walk over the 33 row starts held in shared memory, and per-row positions
+// come from ballots over the row segments of the 32 lanes (no atomics).
+//
+// Binning (Sec. 4.3 co-optimisation): d+ < 2 is skipped (no triangle can be
+// closed), 2 <= d+ <= T_w goes to the warp-worker list, d+ > T_w becomes
+// ceil(d+ / item_neighbors) thread-block work items (u, first neighbour).
+#include "tc_internal.h"
+
+namespace tcg {
+
+namespace {
+
+__device__ __forceinline__ unsigned lanemask_le(int lane) { return (2u << lane) - 1u; }
+__device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
+
+template <typename Off>
+__global__ void k_degree(const Off* __restrict__ row_ptr, int64_t n, int64_t nnz, int32_t* __restrict__ deg,
+                         DevCounters* ctr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        const long long a = (long long)row_ptr[u], b = (long long)row_ptr[u + 1];
+        long long d = b - a;
+        if (a < 0 || d < 0 || b > nnz || d > 0x7fffffffLL) {
+            atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
+            d = 0;
+        }
+        deg[u] = (int32_t)d;
+    }
+}
+
+constexpr int ORIENT_THREADS = 256;
+constexpr int ORIENT_WARPS = ORIENT_THREADS / 32;
+
+// COMPACT == false: kept[u] = out-degree. COMPACT == true: write dag_col.
+template <typename Off, bool COMPACT>
+__global__ void __launch_bounds__(ORIENT_THREADS)
+    k_orient(const Off* __restrict__ row_ptr, const int32_t* __restrict__ col, const int32_t* __restrict__ deg,
+             int64_t n, int64_t nnz, int32_t* __restrict__ kept, const int32_t* __restrict__ dag_ptr,
+             int32_t* __restrict__ dag_col, int64_t dag_cap, DevCounters* ctr) {
+    __shared__ long long s_st[ORIENT_WARPS][33];
+    __shared__ int s_cnt[ORIENT_WARPS][32];
+    __shared__ int s_dp[ORIENT_WARPS][32];
+    if (COMPACT && ctr->err) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned le = lanemask_le(lane), lt = lanemask_lt(lane);
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    long long* st = s_st[w];
+    int* cnt = s_cnt[w];
+    int* dp = s_dp[w];
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g * 32 < n; g += nw) {
+        const int64_t u0 = g * 32;
+        const int nr = (int)(n - u0 < 32 ? n - u0 : 32);
+        long long e = 0;
+        if (lane == 0) e = (long long)row_ptr[u0 + nr];
+        e = __shfl_sync(FULL, e, 0);
+        long long a = (lane < nr) ? (long long)row_ptr[u0 + lane] : e;
+        long long nx = __shfl_down_sync(FULL, a, 1);
+        if (lane == 31) nx = e;
+        const bool bad = (lane < nr) && (a < 0 || nx < a || nx > nnz);
+        if (__any_sync(FULL, bad)) {
+            if (lane == 0) atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
+            continue;
+        }
+        st[lane] = a;
+        if (lane == 0) st[32] = e;
+        cnt[lane] = 0;
+        if (COMPACT) dp[lane] = (lane < nr) ? dag_ptr[u0 + lane] : 0;
+        __syncwarp();
+        const long long gb = __shfl_sync(FULL, a, 0), ge = e;
+        int r = 0;
+        for (long long base = gb; base < ge; base += 32) {
+            const long long f = base + lane;
+            const bool act = f < ge;
+            bool keep = false;
+            int v = 0;
+            if (act) {
+                while (st[r + 1] <= f) ++r;
+                v = col[f];
+                if ((unsigned)v >= (unsigned long long)n) {
+                    atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
+                } else {
+                    const int du = (int)(st[r + 1] - st[r]);
+                    const int dv = deg[v];
+                    keep = (dv > du) || (dv == du && (int64_t)v > u0 + r);
+                }
+            }
+            const unsigned km = __ballot_sync(FULL, keep);
+            const unsigned am = __ballot_sync(FULL, act);
+            const int rp = __shfl_up_sync(FULL, r, 1);
+            const int rn = __shfl_down_sync(FULL, r, 1);
+            const bool seg_start = act && (lane == 0 || rp != r);
+            const bool seg_end = act && (lane == 31 || !((am >> (lane + 1)) & 1u) || rn != r);
+            const unsigned sm = __ballot_sync(FULL, seg_start);
+            unsigned segbits = 0;
+            if (act) {
+                const int first = 31 - __clz(sm & le);
+                segbits = ~((1u << first) - 1u);
+            }
+            if (COMPACT && keep) {
+                const long long pos = (long long)dp[r] + cnt[r] + __popc(km & lt & segbits);
+                if (pos < dag_cap)
+                    dag_col[pos] = v;
+                else
+                    atomicOr(&ctr->err, ERRBIT_DAG_OVERFLOW);
+            }
+            __syncwarp();
+            if (seg_end) cnt[r] += __popc(km & le & segbits);
+            __syncwarp();
+        }
+        if (!COMPACT && lane < nr) kept[u0 + lane] = cnt[lane];
+        __syncwarp();
+    }
+}
+
+// ---- exclusive scan of int32 counts with an int64 carry ---------------------
+
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_ITEMS = 16;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;  // 8192
+constexpr int SCAN_TOP_THREADS = 1024;
+
+__device__ __forceinline__ long long warp_incl_scan(long long v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long t = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Exclusive block scan; returns the exclusive prefix, *total = block sum.
+__device__ __forceinline__ long long block_excl_scan(long long v, long long* sh, long long* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const long long inc = warp_incl_scan(v, lane);
+    if (lane == 31) sh[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const long long x = (lane < nw) ? sh[lane] : 0;
+        const long long xi = warp_incl_scan(x, lane);
+        if (lane < nw) sh[lane] = xi - x;
+        if (lane == 31) sh[32] = xi;
+    }
+    __syncthreads();
+    const long long r = sh[w] + inc - v;
+    *total = sh[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS)
+    k_scan_reduce(const int32_t* __restrict__ in, int64_t n, long long* __restrict__ partial) {
+    __shared__ long long sh[33];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    long long s = 0;
+    for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS) {
+        const int64_t k = base + i;
+        if (k < n) s += in[k];
+    }
+    long long tot;
+    block_excl_scan(s, sh, &tot);
+    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(SCAN_TOP_THREADS)
+    k_scan_top(long long* __restrict__ partial, int nb, int32_t* __restrict__ out, int64_t n, DevCounters* ctr) {
+    __shared__ long long sh[33];
+    const int per = (nb + SCAN_TOP_THREADS - 1) / SCAN_TOP_THREADS;
+    const int b0 = threadIdx.x * per, b1 = min(nb, b0 + per);
+    long long s = 0;
+    for (int i = b0; i < b1; ++i) s += partial[i];
+    long long tot;
+    long long pre = block_excl_scan(s, sh, &tot);
+    for (int i = b0; i < b1; ++i) {
+        const long long x = partial[i];
+        partial[i] = pre;
+        pre += x;
+    }
+    if (threadIdx.x == 0) {
+        ctr->m = tot;
+        if (tot > 0x7fffffffLL) atomicOr(&ctr->err, ERRBIT_DAG_TOO_BIG);
+        out[n] = (int32_t)tot;
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS)
+    k_scan_down(const int32_t* __restrict__ in, int64_t n, const long long* __restrict__ partial,
+                int32_t* __restrict__ out) {
+    __shared__ int s_tile[SCAN_TILE];
+    __shared__ long long sh[33];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS) {
+        const int64_t k = base + i;
+        s_tile[i] = (k < n) ? in[k] : 0;
+    }
+    __syncthreads();
+    int* mine = s_tile + threadIdx.x * SCAN_ITEMS;
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) s += mine[i];
+    long long tot;
+    long long pre = block_excl_scan(s, sh, &tot) + partial[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        const int x = mine[i];
+        mine[i] = (int)pre;  // exceeds int32 only when ERRBIT_DAG_TOO_BIG is raised
+        pre += x;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS) {
+        const int64_t k = base + i;
+        if (k < n) out[k] = s_tile[i];
+    }
+}
+
+// ---- binning ----------------------------------------------------------------
+
+__global__ void k_bin(const int32_t* __restrict__ dag_ptr, int64_t n, int warp_max, int item_nbrs, int shard_count,
+                      int shard_index, int32_t* __restrict__ warp_list, int2* __restrict__ items, int64_t item_cap,
+                      DevCounters* ctr) {
+    if (ctr->err) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t u = base + threadIdx.x;
+        int d = 0;
+        if (u < n && (shard_count <= 1 || (int)(u % shard_count) == shard_index)) d = dag_ptr[u + 1] - dag_ptr[u];
+        const bool is_warp = d >= 2 && d <= warp_max;
+        const unsigned wm = __ballot_sync(FULL, is_warp);
+        if (wm) {
+            const int leader = __ffs(wm) - 1;
+            int pos = 0;
+            if (lane == leader) pos = atomicAdd(&ctr->n_warp, __popc(wm));
+            pos = __shfl_sync(FULL, pos, leader);
+            if (is_warp) warp_list[pos + __popc(wm & lanemask_lt(lane))] = (int32_t)u;
+        }
+        if (d > warp_max) {
+            const int k = (d + item_nbrs - 1) / item_nbrs;
+            atomicAdd(&ctr->n_block, 1);
+            const int pos = atomicAdd(&ctr->n_items, k);
+            if ((int64_t)pos + k <= item_cap) {
+                for (int j = 0; j < k; ++j) items[pos + j] = make_int2((int)u, j * item_nbrs);
+            } else {
+                atomicOr(&ctr->err, ERRBIT_DAG_OVERFLOW);
+            }
+        }
+    }
+}
+
+template <typename Off>
+cudaError_t orient_t(const Off* row_ptr, const int32_t* col, int64_t n, int64_t nnz, int32_t* deg, int32_t* kept,
+                     long long* partial, int32_t* dag_ptr, int32_t* dag_col, int64_t dag_cap, DevCounters* ctr,
+                     int num_sms, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t groups = (n + 31) / 32;
+    int og = (int)((groups + ORIENT_WARPS - 1) / ORIENT_WARPS);
+    const int og_cap = num_sms * 8 * 4;
+    if (og > og_cap) og = og_cap;
+    int dg = (int)((n + 255) / 256);
+    if (dg > num_sms * 16) dg = num_sms * 16;
+    k_degree<Off><<<dg, 256, 0, st>>>(row_ptr, n, nnz, deg, ctr);
+    k_orient<Off, false><<<og, ORIENT_THREADS, 0, st>>>(row_ptr, col, deg, n, nnz, kept, nullptr, nullptr, 0, ctr);
+    const int nb = scan_blocks(n);
+    k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(kept, n, partial);
+    k_scan_top<<<1, SCAN_TOP_THREADS, 0, st>>>(partial, nb, dag_ptr, n, ctr);
+    k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(kept, n, partial, dag_ptr);
+    k_orient<Off, true><<<og, ORIENT_THREADS, 0, st>>>(row_ptr, col, deg, n, nnz, nullptr, dag_ptr, dag_col, dag_cap,
+                                                       ctr);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int scan_blocks(int64_t n) { return (int)((n + SCAN_TILE - 1) / SCAN_TILE); }
+
+cudaError_t launch_orient(const void* row_ptr, int offset_bits, const int32_t* col, int64_t n, int64_t nnz,
+                          int32_t* deg, int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
+                          int64_t dag_cap, DevCounters* ctr, int num_sms, cudaStream_t st) {
+    if (offset_bits == 64)
+        return orient_t(static_cast<const long long*>(row_ptr), col, n, nnz, deg, kept, partial, dag_ptr, dag_col,
+                        dag_cap, ctr, num_sms, st);
+    return orient_t(static_cast<const int32_t*>(row_ptr), col, n, nnz, deg, kept, partial, dag_ptr, dag_col, dag_cap,
+                    ctr, num_sms, st);
+}
+
+cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* items,
+                       int64_t item_cap, DevCounters* ctr, int num_sms, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int g = (int)((n + 255) / 256);
+    if (g > num_sms * 16) g = num_sms * 16;
+    k_bin<<<g, 256, 0, st>>>(dag_ptr, n, cfg.warp_max_out_degree, cfg.item_neighbors, cfg.shard_count,
+                             cfg.shard_index, warp_list, items, item_cap, ctr);
+    return cudaGetLastError();
+}
+
+}  // namespace tcg

@@ -1,0 +1,91 @@
+// tc_internal.h -- shared declarations of the CUDA library (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tc.h"
+
+namespace tcg {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Error bits the kernels raise in DevCounters::err (host maps them to tc_status).
+enum : int {
+    ERRBIT_BAD_GRAPH = 1,    // column id out of range, row_ptr not monotone / out of [0, nnz]
+    ERRBIT_DAG_TOO_BIG = 2,  // m >= 2^31 (int32 DAG offsets)
+    ERRBIT_DAG_OVERFLOW = 4, // more kept edges than the DAG buffer holds (asymmetric input)
+};
+
+// Device-resident scalars of one counting pass. Zeroed (cudaMemsetAsync)
+// before each pass.
+struct DevCounters {
+    unsigned long long total;  // triangle count
+    long long m;               // DAG edges (scan total)
+    int n_warp;                // vertices in the warp-worker list
+    int n_items;               // work items of thread-block workers
+    int n_block;               // vertices with d+ > warp threshold
+    int q_warp;                // queue cursors (atomic chunk pops, Sec. 4.3)
+    int q_items;
+    int err;                   // ERRBIT_* flags
+    int pad[6];
+};
+static_assert(sizeof(DevCounters) == 64, "DevCounters layout");
+
+// Resolved launch parameters (host fills from tc_params + device properties).
+struct CountCfg {
+    int warp_max_out_degree;   // T_w
+    int warp_table_ints;       // per-warp table capacity
+    int warp_max_buckets;      // power of two
+    int max_levels;            // L cap
+    int warps_per_block;       // warp kernel
+    int warp_grid;             // persistent grid of the warp kernel
+    int block_threads;         // block kernel
+    int block_smem_bytes;
+    int block_grid;
+    int item_neighbors;
+    int chunk;
+    int shard_count, shard_index;
+};
+
+// ---- orientation (orient.cu) ----------------------------------------------
+// deg, kept: int32[n]; partial: int64[scan_blocks(n)+1]; dag_ptr: int32[n+1];
+// warp_list: int32[n]; items: int2[item_cap].
+int scan_blocks(int64_t n);
+cudaError_t launch_orient(const void* row_ptr, int offset_bits, const int32_t* col, int64_t n, int64_t nnz,
+                          int32_t* deg, int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
+                          int64_t dag_cap, DevCounters* ctr, int num_sms, cudaStream_t st);
+
+// Binning (Sec. 4.3) from an existing DAG: fills warp_list / items / counters.
+cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* items,
+                       int64_t item_cap, DevCounters* ctr, int num_sms, cudaStream_t st);
+
+// ---- counting (count.cu) ----------------------------------------------------
+cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t n, const int32_t* warp_list,
+                         const int2* items, unsigned long long* per_vertex, const CountCfg& cfg, DevCounters* ctr,
+                         cudaStream_t st);
+cudaError_t count_kernel_setup(CountCfg& cfg, int num_sms);
+cudaError_t launch_finish(const DevCounters* ctr, unsigned long long* count_out, int* err_out, cudaStream_t st);
+
+// stats: W+ (total and block part), max d+
+struct DevStats {
+    unsigned long long wplus, wplus_block;
+    long long max_out;
+    long long n_skip, n_warp, n_block;
+};
+cudaError_t launch_stats(const int32_t* dag_ptr, const int32_t* dag_col, int64_t n, int warp_max_out_degree,
+                         DevStats* out, cudaStream_t st);
+
+// Upper bound on work items produced by binning (one per large vertex plus
+// one per item_neighbors of its out-list).
+inline int64_t item_capacity(int64_t n, int64_t m, int item_neighbors) {
+    return n + m / (item_neighbors > 0 ? item_neighbors : 1) + 1;
+}
+
+__host__ __device__ inline int next_pow2(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+}  // namespace tcg

@@ -1,0 +1,79 @@
+"""The C-ABI library builds, loads and exports what include/tc.h declares.
+
+No compute call is made here (these run without a GPU).
+"""
+import ast
+import glob
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def tc():
+    import __graft_entry__ as ge
+    ge._load_builder().build()
+    from paper_2103_08053_gb300 import _tc
+    return _tc
+
+
+def test_every_declared_symbol_is_exported(tc):
+    names = tc.declared_functions()
+    assert len(names) >= 20
+    missing = [n for n in names if not tc.exported(n)]
+    assert not missing, missing
+    for core in ("tc_orient", "tc_count", "tc_count_batch", "tc_submit", "tc_poll"):
+        assert core in names
+
+
+def test_status_strings(tc):
+    for code in range(9):
+        s = tc.tc_status_string(code).decode()
+        assert s.startswith("TC_")
+    assert tc.tc_status_string(99).decode() == "unknown tc_status"
+    assert b"sm_103a" in tc.tc_version()
+
+
+def test_default_params(tc):
+    import paper_2103_08053_gb300 as T
+    p = T.default_params()
+    assert p["warp_max_buckets"] & (p["warp_max_buckets"] - 1) == 0
+    assert p["max_levels"] == 128          # the paper's maximum collision count
+    assert p["shard_count"] == 1 and p["shard_index"] == 0
+
+
+def test_null_arguments_rejected_without_gpu(tc):
+    import ctypes
+    assert tc.tc_count(None, None, None, None) == tc.TC_ERR_INVALID_ARG
+    assert tc.tc_destroy(None) == tc.TC_OK
+    assert tc.tc_default_params(None) == tc.TC_ERR_INVALID_ARG
+    assert tc.tc_last_error(None) == b""
+
+
+def test_create_fails_cleanly_without_gpu(tc):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import ctypes
+    h = ctypes.c_void_p()
+    assert tc.tc_create(ctypes.byref(h), 0, 0, None) == tc.TC_ERR_CUDA
+
+
+def test_product_package_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2103_08053_gb300")
+    for path in glob.glob(os.path.join(pkg, "**", "*.py"), recursive=True):
+        tree = ast.parse(open(path).read())
+        for node in ast.walk(tree):
+            if isinstance(node, ast.Import):
+                assert not any(a.name.split(".")[0] == "oracle" for a in node.names), path
+            if isinstance(node, ast.ImportFrom):
+                assert (node.module or "").split(".")[0] != "oracle", path
+    for path in glob.glob(os.path.join(pkg, "csrc", "*")):
+        assert "oracle" not in open(path).read().lower(), path
+
+
+def test_oracle_and_cuda_share_no_sources():
+    orc = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
+    assert "#include \"tc" not in orc and "tc_internal" not in orc

@@ -1,0 +1,279 @@
+"""CUDA path vs the CPU oracle, through the C ABI (bit-exact: counts are integers).
+
+Inputs come from graphgen (seeded). Sizes span several scan tiles (8192
+rows), several 32-row orientation groups with a ragged tail, warp and block
+workers, multi-item and multi-part block work, and table overflow.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import graphgen as G
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    import __graft_entry__ as ge
+    ge._load_builder().build()
+    import paper_2103_08053_gb300 as T
+    return T
+
+
+@pytest.fixture(scope="module")
+def ctx(T):
+    c = T.Context(0)
+    yield c
+    c.close()
+
+
+def dev(g, bits=32):
+    d = torch.device("cuda", 0)
+    rp = torch.from_numpy(g.row_ptr.astype(np.int64 if bits == 64 else np.int32)).to(d)
+    col = torch.from_numpy(np.ascontiguousarray(g.col, dtype=np.int32)).to(d)
+    return rp, col
+
+
+def gpu_count(ctx, g, bits=32):
+    rp, col = dev(g, bits)
+    return ctx.count(g.n, rp, col)
+
+
+# ------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("make,want", [
+    (lambda: G.complete(3), 1), (lambda: G.complete(40), math.comb(40, 3)),
+    (lambda: G.complete(200), math.comb(200, 3)),      # d+ up to 199 -> block worker
+    (lambda: G.cycle(3), 1), (lambda: G.cycle(1000), 0), (lambda: G.wheel(500), 500),
+    (lambda: G.friendship(300), 300), (lambda: G.complete_bipartite(40, 60), 0),
+    (lambda: G.grid2d(70, 90), 0), (lambda: G.torus3d(20), 0), (lambda: G.torus3d(3), 27),
+    (lambda: G.star(5000), 0), (lambda: G.empty(7), 0),
+])
+def test_closed_forms(ctx, make, want):
+    g = make()
+    assert gpu_count(ctx, g) == want
+    assert gpu_count(ctx, g, 64) == want
+
+
+def test_tiny_and_empty(ctx):
+    assert gpu_count(ctx, G.empty(0)) == 0
+    assert gpu_count(ctx, G.empty(1)) == 0
+    g = G.from_edge_list(2, [(0, 1)])
+    assert gpu_count(ctx, g) == 0
+
+
+# ----------------------------------------------------------- random graphs
+
+@pytest.mark.parametrize("n,p,seed", [(30, 0.3, 1), (150, 0.2, 2), (200, 0.6, 3), (333, 0.05, 4)])
+def test_random_small_vs_brute(ctx, n, p, seed):
+    g = G.random_small(n, p, seed)
+    want = oracle.brute(g)
+    assert oracle.count(g) == want
+    assert gpu_count(ctx, g) == want
+
+
+@pytest.mark.parametrize("scale,ef,seed", [(8, 8, 1), (10, 16, 2), (13, 16, 3), (14, 4, 4), (15, 32, 5)])
+def test_rmat_vs_oracle(ctx, scale, ef, seed):
+    g = G.rmat(scale, ef, seed=seed)
+    want = oracle.count(g)
+    assert gpu_count(ctx, g) == want
+    assert gpu_count(ctx, g, 64) == want
+
+
+@pytest.mark.parametrize("n,seed", [(25_001, 6), (70_000, 7)])
+def test_rgg_ragged_vs_oracle(ctx, n, seed):
+    g = G.rgg(n, 48.0, seed=seed)
+    assert gpu_count(ctx, g) == oracle.count(g)
+
+
+def test_er_vs_oracle(ctx):
+    g = G.erdos_renyi(20_011, 0.003, seed=8)
+    assert gpu_count(ctx, g) == oracle.count(g)
+
+
+def test_unsorted_rows_and_relabel(ctx):
+    g = G.rmat(12, 16, seed=9)
+    want = oracle.count(g)
+    assert gpu_count(ctx, G.shuffle_rows(g, 1)) == want
+    perm = np.random.default_rng(2).permutation(g.n)
+    assert gpu_count(ctx, G.relabel(g, perm)) == want
+
+
+def test_disjoint_union(ctx):
+    gs = [G.rmat(9, 8, seed=s) for s in range(4)] + [G.complete(150), G.wheel(64)]
+    u = G.disjoint_union(gs)
+    assert gpu_count(ctx, u) == sum(gpu_count(ctx, g) for g in gs) == oracle.count(u)
+
+
+# --------------------------------------------------------------- the DAG
+
+def test_orientation_matches_oracle(ctx):
+    g = G.rmat(13, 16, seed=10)
+    rp, col = dev(g)
+    d = ctx.orient(g.n, rp, col)
+    od = oracle.orient(g)
+    assert d.m == od.m == g.m
+    dp, dc = d.tensors()
+    assert np.array_equal(dp.cpu().numpy().astype(np.int64), od.dag_ptr)
+    # input rows are sorted and compaction keeps input order -> identical
+    assert np.array_equal(dc.cpu().numpy(), od.dag_col)
+    d.free()
+
+
+def test_orientation_unsorted_rows(ctx):
+    g = G.shuffle_rows(G.rmat(11, 16, seed=11), 3)
+    rp, col = dev(g)
+    d = ctx.orient(g.n, rp, col)
+    od = oracle.orient(g)
+    dp, dc = d.tensors()
+    dp, dc = dp.cpu().numpy(), dc.cpu().numpy()
+    assert np.array_equal(dp.astype(np.int64), od.dag_ptr)
+    for u in range(g.n):
+        assert np.array_equal(np.sort(dc[dp[u]:dp[u + 1]]), od.dag_col[od.dag_ptr[u]:od.dag_ptr[u + 1]])
+    d.free()
+
+
+def test_per_vertex_counts(ctx):
+    g = G.rmat(13, 16, seed=12)
+    rp, col = dev(g)
+    d = ctx.orient(g.n, rp, col)
+    pv = torch.zeros(g.n, dtype=torch.int64, device="cuda")
+    total = ctx.count_dag(d, per_vertex=pv)
+    want_total, want_pv = oracle.count_dag(oracle.orient(g), per_vertex=True)
+    assert total == want_total
+    assert np.array_equal(pv.cpu().numpy().astype(np.uint64), want_pv)
+    st = ctx.dag_stats(d)
+    od = oracle.orient(g)
+    outd = od.out_degrees()
+    assert st["m"] == od.m and st["max_out_degree"] == outd.max()
+    assert st["wedges_plus"] == int(sum(outd[od.dag_col]))
+    assert st["n_skip"] + st["n_warp"] + st["n_block"] == g.n
+    d.free()
+
+
+# ------------------------------------------------------ worker/table regimes
+
+PARAM_SETS = {
+    "tiny_levels": dict(max_levels=2),                         # overflow chains everywhere
+    "all_block": dict(warp_max_out_degree=1),                  # every vertex on the block path
+    "all_warp": dict(warp_max_out_degree=2000, warp_table_ints=4096, warp_max_buckets=1024, warps_per_block=4),
+    "small_items": dict(item_neighbors=32, warp_max_out_degree=16),
+    "split_parts": dict(block_threads=64, block_smem_bytes=4096, warp_max_out_degree=8),  # part_max = 256
+    "chunk7": dict(chunk=7),
+}
+
+
+@pytest.mark.parametrize("name", sorted(PARAM_SETS))
+def test_param_regimes(T, name):
+    gs = [G.rmat(14, 16, seed=13), G.complete(300), G.rgg(30_000, 40.0, seed=14)]
+    with T.Context(0, params=PARAM_SETS[name]) as c:
+        for g in gs:
+            assert gpu_count(c, g) == oracle.count(g), (name, g.name)
+
+
+def _bucket_collision_graph(k, stride=1024):
+    # u = 0 joined to k vertices whose ids are multiples of `stride`, which form
+    # a clique: every key of N+(0) hashes to bucket 0 for any B <= stride.
+    hub = [stride * (i + 1) for i in range(k)]
+    n = stride * (k + 1) + 1
+    e = [(0, h) for h in hub] + [(a, b) for i, a in enumerate(hub) for b in hub[i + 1:]]
+    return G.from_edge_list(n, e)
+
+
+@pytest.mark.parametrize("k,params", [(60, {}), (300, {}), (60, dict(max_levels=3)),
+                                      (300, dict(max_levels=2)), (500, dict(block_threads=64,
+                                                                            block_smem_bytes=4096))])
+def test_adversarial_overflow(T, k, params):
+    g = _bucket_collision_graph(k)
+    want = math.comb(k, 2) + math.comb(k, 3)
+    assert oracle.count(g) == want
+    with T.Context(0, params=params) as c:
+        assert gpu_count(c, g) == want
+
+
+def test_shards_sum_to_total(T):
+    g = G.rmat(13, 16, seed=15)
+    want = oracle.count(g)
+    parts = []
+    for i in range(3):
+        with T.Context(0, params=dict(shard_count=3, shard_index=i)) as c:
+            parts.append(gpu_count(c, g))
+    assert sum(parts) == want and all(p > 0 for p in parts)
+
+
+# ------------------------------------------------------------ entry points
+
+def test_count_async_and_host(ctx):
+    g = G.rmat(12, 16, seed=16)
+    want = oracle.count(g)
+    rp, col = dev(g)
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    err = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    ctx.count_async(g.n, rp, col, out, err)
+    torch.cuda.synchronize()
+    assert int(out.item()) == want and int(err.item()) == 0
+    assert ctx.count_host(g.n, g.row_ptr, g.col) == want
+    assert ctx.count_host(g.n, g.row_ptr.astype(np.int32), g.col) == want
+
+
+def test_repeated_calls_are_identical(ctx):
+    g = G.rmat(14, 16, seed=17)
+    rp, col = dev(g)
+    vals = {ctx.count(g.n, rp, col) for _ in range(5)}
+    assert vals == {oracle.count(g)}
+
+
+# ------------------------------------------------------------- bad inputs
+
+def test_bad_column_id(T, ctx):
+    g = G.rmat(10, 8, seed=18)
+    col = g.col.copy()
+    col[17] = g.n + 5
+    rp, c = dev(G.Csr(g.n, g.row_ptr, col))
+    with pytest.raises(T.TcError) as ei:
+        ctx.count(g.n, rp, c)
+    assert ei.value.status == T.TC_ERR_BAD_GRAPH
+    col[17] = -3
+    rp, c = dev(G.Csr(g.n, g.row_ptr, col))
+    with pytest.raises(T.TcError):
+        ctx.count(g.n, rp, c)
+    # the context stays usable
+    assert gpu_count(ctx, g) == oracle.count(g)
+
+
+def test_bad_row_ptr(T, ctx):
+    g = G.rmat(10, 8, seed=19)
+    rp = g.row_ptr.copy()
+    rp[100] = rp[101] + 5        # not monotone
+    with pytest.raises(T.TcError) as ei:
+        ctx.count(g.n, *dev(G.Csr(g.n, rp, g.col)))
+    assert ei.value.status == T.TC_ERR_BAD_GRAPH
+    rp = g.row_ptr.copy()
+    rp[-1] = rp[-1] + 1000       # beyond nnz
+    with pytest.raises(T.TcError):
+        ctx.count(g.n, *dev(G.Csr(g.n, rp, g.col)))
+
+
+def test_asymmetric_input_does_not_overflow(T, ctx):
+    # Every row has 10 entries (forward ids, padded with self-loops), so all
+    # degrees tie and every forward entry is kept: m would exceed nnz/2.
+    n, d = 1000, 10
+    rows = [[v if v < n else u for v in range(u + 1, u + 1 + d)] for u in range(n)]
+    rp = np.arange(0, n * d + 1, d, dtype=np.int64)
+    col = np.array(rows, dtype=np.int32).ravel()
+    with pytest.raises(T.TcError) as ei:
+        ctx.count(n, *dev(G.Csr(n, rp, col)))
+    assert ei.value.status == T.TC_ERR_BAD_GRAPH
+    assert gpu_count(ctx, G.complete(10)) == 120
+
+
+def test_invalid_params(T):
+    for bad in (dict(warp_max_buckets=48), dict(max_levels=1), dict(shard_count=2, shard_index=2),
+                dict(warp_max_out_degree=5000), dict(block_threads=100)):
+        with pytest.raises(T.TcError) as ei:
+            T.Context(0, params=bad)
+        assert ei.value.status == T.TC_ERR_INVALID_ARG
