@@ -30,15 +30,15 @@
  *     stream). Device inputs must stay valid and unmodified until the call
  *     returns (blocking calls) or until the stream reaches the call's work
  *     (the *_async calls).
- *   - A context is not thread-safe, except tc_submit / tc_poll / tc_cancel,
+ *   - A context is not thread-safe, except tc_submit / tc_poll / tc_drain,
  *     which may be called from any thread at any time.
  *
  * Input preconditions (not all checked): the CSR is symmetric (v in N(u) iff
  * u in N(v)) with no duplicate entries in a row; rows need not be sorted;
- * self-loops are allowed and ignored (the strict order drops u -> u). Column
- * ids outside [0, n) are always detected and reported as TC_ERR_BAD_GRAPH.
- * With tc_params.validate = 1 the library also checks row_ptr monotonicity
- * and symmetry-implied sizes before counting.
+ * self-loops are allowed and ignored (the strict order drops u -> u). Always
+ * detected and reported as TC_ERR_BAD_GRAPH, without faulting: column ids
+ * outside [0, n), row_ptr not non-decreasing within [0, nnz], and more kept
+ * edges than nnz/2 (an asymmetric CSR).
  */
 #ifndef TRUST_GB300_TC_H
 #define TRUST_GB300_TC_H
@@ -93,18 +93,19 @@ typedef struct {
 /* Tunables. Zero in any field means "use the default" (tc_default_params).
  * The paper's constants are noted beside each (Sec. 3.1, 3.2, 4.3). */
 typedef struct {
-    int32_t warp_max_out_degree; /* d+ above this -> thread-block worker (paper: 100; default 128) */
-    int32_t warp_table_ints;     /* per-warp hash table capacity, ints (paper: 32 buckets x 6 levels in smem) */
-    int32_t warp_max_buckets;    /* bucket count cap for warp tables (power of two; paper: 32) */
-    int32_t max_levels;          /* maximum collision count L of a bucket before overflow (paper: 128) */
+    int32_t warp_max_out_degree; /* d+ above this -> thread-block worker, <= 255 (paper: 100; default 128) */
+    int32_t warp_area_ints;      /* shared-memory table area of one warp worker, ints (default 1088);
+                                    a warp-worker table has B = 2*nextpow2(d+) buckets of 4 slots */
+    int32_t warp_min_buckets;    /* fewest buckets of a warp-worker table, power of two >= 16 (default 16) */
+    int32_t max_levels;          /* cap on the levels of a thread-block table (paper's max collision: 128) */
     int32_t block_threads;       /* threads of a thread-block worker (default 1024) */
     int32_t block_smem_bytes;    /* shared memory of a thread-block worker (default 200 KiB) */
     int32_t item_neighbors;      /* out-neighbours of a large vertex per work item (default 1024) */
-    int32_t chunk;               /* vertices a warp takes per queue pop (Sec. 4.3; paper: 1..7) */
+    int32_t chunk;               /* vertices a warp takes per queue pop, 1..32 (Sec. 4.3; paper: 1..7; default 32) */
     int32_t warps_per_block;     /* warps per block of the warp-worker kernel (default 8) */
     int32_t shard_count;         /* workload partition (Sec. 5.1): count only u with */
     int32_t shard_index;         /*   u % shard_count == shard_index (default 1 / 0) */
-    int32_t validate;            /* 1: check row_ptr monotonicity on the device first */
+    int32_t validate;            /* reserved for extra input checks (0) */
     int32_t reserved[4];
 } tc_params;
 
@@ -206,7 +207,8 @@ tc_status tc_drain(tc_ctx* ctx);
 /* ---- diagnostics ---------------------------------------------------------- */
 
 const char* tc_status_string(tc_status s);
-/* Text of the last failure on ctx (empty if none). Valid until the next call. */
+/* Text of the last failure on ctx (empty if none); with ctx == NULL, the last
+ * tc_create failure of the calling thread. Valid until the next call. */
 const char* tc_last_error(tc_ctx* ctx);
 /* Library version string. */
 const char* tc_version(void);

@@ -118,7 +118,7 @@ class Context:
         p = _params_struct(params)
         st = _tc.tc_create(ctypes.byref(h), device, mem_budget, ctypes.byref(p) if p is not None else None)
         if st != TC_OK:
-            raise TcError(st, "tc_create failed")
+            raise TcError(st, "tc_create: " + _tc.tc_last_error(None).decode(errors="replace"))
         self.handle = h
 
     def close(self):

@@ -47,7 +47,7 @@ class tc_dag(ctypes.Structure):
 
 
 class tc_params(ctypes.Structure):
-    _fields_ = [("warp_max_out_degree", c_int32), ("warp_table_ints", c_int32), ("warp_max_buckets", c_int32),
+    _fields_ = [("warp_max_out_degree", c_int32), ("warp_area_ints", c_int32), ("warp_min_buckets", c_int32),
                 ("max_levels", c_int32), ("block_threads", c_int32), ("block_smem_bytes", c_int32),
                 ("item_neighbors", c_int32), ("chunk", c_int32), ("warps_per_block", c_int32),
                 ("shard_count", c_int32), ("shard_index", c_int32), ("validate", c_int32),

@@ -12,13 +12,16 @@ using namespace tcg;
 
 // ---------------------------------------------------------------- helpers
 
+// Failures of calls that have no context yet (tc_create) are kept per thread
+// and reported by tc_last_error(NULL).
+static thread_local char g_create_error[512];
+
 tc_status tcg::ctx_fail(tc_ctx* ctx, tc_status s, const char* fmt, ...) {
-    if (ctx) {
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(ctx->last_error, sizeof(ctx->last_error), fmt, ap);
-        va_end(ap);
-    }
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx ? ctx->last_error : g_create_error, ctx ? sizeof(ctx->last_error) : sizeof(g_create_error), fmt,
+              ap);
+    va_end(ap);
     return s;
 }
 
@@ -88,13 +91,13 @@ DeviceGuard::~DeviceGuard() {
 static void fill_defaults(tc_params* p) {
     memset(p, 0, sizeof(*p));
     p->warp_max_out_degree = 128;
-    p->warp_table_ints = 1024;
-    p->warp_max_buckets = 128;
+    p->warp_area_ints = 1088;
+    p->warp_min_buckets = 16;
     p->max_levels = 128;
     p->block_threads = 1024;
     p->block_smem_bytes = 200 * 1024;
     p->item_neighbors = 1024;
-    p->chunk = 4;
+    p->chunk = 32;
     p->warps_per_block = 8;
     p->shard_count = 1;
     p->shard_index = 0;
@@ -112,8 +115,8 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
 #define TAKE(f) \
     if (in->f) p.f = in->f
         TAKE(warp_max_out_degree);
-        TAKE(warp_table_ints);
-        TAKE(warp_max_buckets);
+        TAKE(warp_area_ints);
+        TAKE(warp_min_buckets);
         TAKE(max_levels);
         TAKE(block_threads);
         TAKE(block_smem_bytes);
@@ -125,18 +128,19 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         p.validate = in->validate;
 #undef TAKE
     }
-    if (p.warp_max_out_degree < 1) return ctx_fail(ctx, TC_ERR_INVALID_ARG, "warp_max_out_degree < 1");
-    if (!is_pow2(p.warp_max_buckets) || p.warp_max_buckets < 32)
-        return ctx_fail(ctx, TC_ERR_INVALID_ARG, "warp_max_buckets must be a power of two >= 32");
-    if (p.warp_table_ints < 2 * p.warp_max_buckets)
-        return ctx_fail(ctx, TC_ERR_INVALID_ARG, "warp_table_ints must be >= 2 * warp_max_buckets");
+    if (p.warp_max_out_degree < 1 || p.warp_max_out_degree > 255)
+        return ctx_fail(ctx, TC_ERR_INVALID_ARG, "warp_max_out_degree must be in [1, 255]");
+    if (!is_pow2(p.warp_min_buckets) || p.warp_min_buckets < 16 || p.warp_min_buckets > 4096)
+        return ctx_fail(ctx, TC_ERR_INVALID_ARG, "warp_min_buckets must be a power of two in [16, 4096]");
     if (p.max_levels < 2) return ctx_fail(ctx, TC_ERR_INVALID_ARG, "max_levels must be >= 2");
+    if (p.warp_area_ints < 16 || p.warp_area_ints % 4)
+        return ctx_fail(ctx, TC_ERR_INVALID_ARG, "warp_area_ints must be a multiple of 4");
     {
-        const int lw = p.warp_table_ints / p.warp_max_buckets;
-        const long long cap = (long long)p.warp_max_buckets * (lw < p.max_levels ? lw : p.max_levels);
-        if (cap <= p.warp_max_out_degree)
+        const long long need = pack_table_ints(p.warp_max_out_degree, p.warp_min_buckets);
+        if (need > p.warp_area_ints)
             return ctx_fail(ctx, TC_ERR_INVALID_ARG,
-                            "warp table capacity %lld must exceed warp_max_out_degree %d", cap, p.warp_max_out_degree);
+                            "warp_area_ints %d cannot hold the table of a vertex with d+ = %d (%lld ints)",
+                            p.warp_area_ints, p.warp_max_out_degree, need);
     }
     if (p.block_threads < 64 || p.block_threads > 1024 || p.block_threads % 32)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [64, 1024]");
@@ -144,22 +148,23 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "warps_per_block must be in [1, 32]");
     if (p.item_neighbors < 32 || p.item_neighbors % 32)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "item_neighbors must be a positive multiple of 32");
-    if (p.chunk < 1) return ctx_fail(ctx, TC_ERR_INVALID_ARG, "chunk must be >= 1");
+    if (p.chunk < 1 || p.chunk > 32) return ctx_fail(ctx, TC_ERR_INVALID_ARG, "chunk must be in [1, 32]");
     if (p.shard_count < 1 || p.shard_index < 0 || p.shard_index >= p.shard_count)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "need 0 <= shard_index < shard_count");
     const int max_smem = ctx ? ctx->max_smem_optin : 227 * 1024;
     const long long warp_smem =
-        (long long)p.warps_per_block * (p.warp_max_buckets + p.warp_table_ints + 64) * 4;
+        (long long)p.warps_per_block * (p.warp_area_ints + 160) * 4;
     if (warp_smem > max_smem)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "warp kernel needs %lld B of shared memory (max %d)", warp_smem,
                         max_smem);
-    if (p.block_smem_bytes > max_smem || p.block_smem_bytes / 4 - (p.block_threads / 32) * 64 < 96)
+    if (p.block_smem_bytes > max_smem || p.block_smem_bytes % 16 ||
+        p.block_smem_bytes / 4 - (p.block_threads / 32) * 160 < 96)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "block_smem_bytes out of range (max %d)", max_smem);
     if (out) *out = p;
     if (cfg) {
         cfg->warp_max_out_degree = p.warp_max_out_degree;
-        cfg->warp_table_ints = p.warp_table_ints;
-        cfg->warp_max_buckets = p.warp_max_buckets;
+        cfg->warp_area_ints = p.warp_area_ints;
+        cfg->warp_min_buckets = p.warp_min_buckets;
         cfg->max_levels = p.max_levels;
         cfg->warps_per_block = p.warps_per_block;
         cfg->block_threads = p.block_threads;
@@ -191,6 +196,7 @@ tc_status tcg::check_csr(tc_ctx* ctx, const tc_csr* g) {
 tc_status tcg::ensure_count_ws(tc_ctx* ctx, Workspace& ws, int64_t n, int64_t m, cudaStream_t st) {
     tc_status s;
     if ((s = ws.warp_list.ensure(ctx, (size_t)(n + 1) * 4, st))) return s;
+    if ((s = ws.warp_desc.ensure(ctx, (size_t)(n + 1) * 8, st))) return s;
     if ((s = ws.items.ensure(ctx, (size_t)item_capacity(n, m, ctx->cfg.item_neighbors) * sizeof(int2), st)))
         return s;
     if ((s = ws.ctr.ensure(ctx, sizeof(DevCounters) + 64, st))) return s;
@@ -223,10 +229,11 @@ static tc_status enqueue_count(tc_ctx* ctx, Workspace& ws, const int32_t* dag_pt
     if (per_vertex && n > 0) e = cudaMemsetAsync(per_vertex, 0, (size_t)n * 8, st);
     if (e == cudaSuccess && n > 0) {
         const int64_t m_cap = ws.items.bytes / sizeof(int2);
-        e = launch_bin(dag_ptr, n, ctx->cfg, (int32_t*)ws.warp_list.p, (int2*)ws.items.p, m_cap, ctr, ctx->num_sms,
-                       st);
+        e = launch_bin(dag_ptr, n, ctx->cfg, (int32_t*)ws.warp_list.p, (int2*)ws.warp_desc.p, (int2*)ws.items.p,
+                       m_cap, ctr, ctx->num_sms, st);
         if (e == cudaSuccess)
-            e = launch_count(dag_ptr, dag_col, n, (const int32_t*)ws.warp_list.p, (const int2*)ws.items.p,
+            e = launch_count(dag_ptr, dag_col, n, (const int32_t*)ws.warp_list.p, (const int2*)ws.warp_desc.p,
+                             (const int2*)ws.items.p,
                              (unsigned long long*)per_vertex, ctx->cfg, ctr, st);
     }
     return cuda_status(ctx, e, "counting kernels");
@@ -258,9 +265,9 @@ tc_status tc_create(tc_ctx** out, int device, size_t mem_budget_bytes, const tc_
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
-        return TC_ERR_CUDA;
+        return ctx_fail(nullptr, TC_ERR_CUDA, "no CUDA device available");
     }
-    if (device < 0 || device >= ndev) return TC_ERR_INVALID_ARG;
+    if (device < 0 || device >= ndev) return ctx_fail(nullptr, TC_ERR_INVALID_ARG, "device %d out of range", device);
     tc_ctx* ctx = new (std::nothrow) tc_ctx();
     if (!ctx) return TC_ERR_OOM;
     ctx->device = device;
@@ -278,6 +285,7 @@ tc_status tc_create(tc_ctx** out, int device, size_t mem_budget_bytes, const tc_
     if (!s) s = ctx->ws.ctr.ensure(ctx, sizeof(DevCounters) + 64, 0);
     if (!s) s = ctx->out_scalars.ensure(ctx, 64, 0);
     if (s) {
+        memcpy(g_create_error, ctx->last_error, sizeof(g_create_error));
         tc_destroy(ctx);
         return s;
     }
@@ -505,7 +513,7 @@ const char* tc_status_string(tc_status s) {
     return "unknown tc_status";
 }
 
-const char* tc_last_error(tc_ctx* ctx) { return ctx ? ctx->last_error : ""; }
+const char* tc_last_error(tc_ctx* ctx) { return ctx ? ctx->last_error : g_create_error; }
 
 const char* tc_version(void) { return "trust-gb300 0.1 (sm_103a)"; }
 

@@ -26,9 +26,9 @@ struct DevBuf {
 
 // Scratch of one counting pass.
 struct Workspace {
-    DevBuf deg, kept, partial, dag_ptr, dag_col, warp_list, items, ctr, stats;
+    DevBuf deg, kept, partial, dag_ptr, dag_col, warp_list, warp_desc, items, ctr, stats;
     void release_all(tc_ctx* ctx) {
-        for (DevBuf* b : {&deg, &kept, &partial, &dag_ptr, &dag_col, &warp_list, &items, &ctr, &stats})
+        for (DevBuf* b : {&deg, &kept, &partial, &dag_ptr, &dag_col, &warp_list, &warp_desc, &items, &ctr, &stats})
             b->release(ctx);
     }
 };

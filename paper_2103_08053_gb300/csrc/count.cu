@@ -7,47 +7,203 @@
 //     by an atomic increment of the bucket's length (Algorithm 1,
 //     hashTableConstruction; Sec. 3.1);
 //   * hash(x) = x mod B with B a power of two (Algorithm 1, hash);
-//   * level-major ("interleaved") layout: element j of bucket i at j*B + i,
-//     with the lengths in shared memory (Sec. 3.2). Here the whole table is in
-//     shared memory: B and the level count L are sized from d+(u) so that
-//     B*L > d+(u) always holds (see below), so no global spill region exists;
-//   * a bucket holding L elements is full; further keys go to the next bucket
-//     and a search continues through successor buckets while the bucket it
-//     scanned was full (Sec. 3.2, last paragraph: linear probing on overflow);
+//   * a bucket that holds its maximum number of elements is full; further keys
+//     go to the next bucket and a search continues through successor buckets
+//     while the bucket it scanned was full (Sec. 3.2, last paragraph: linear
+//     probing on overflow);
 //   * linear search inside a bucket (Algorithm 1, linearSearch);
-//   * virtual combination (Sec. 4.2): the 2-hop lists N+(v) of 32 consecutive
+//   * virtual combination (Sec. 4.2): the 2-hop lists N+(v) of 32
 //     out-neighbours are treated as one flat array whose indices are dealt to
 //     the 32 lanes; a lane finds the owning list of its index from the
-//     inclusive prefix of the list lengths;
-//   * degree-aware workers (Sec. 4.3): 2 <= d+ <= T_w -> one warp with a
-//     warp-private table; d+ > T_w -> one thread block with a block-wide table,
-//     its out-list split into work items of item_neighbors neighbours; both
-//     pull work from atomic queues in chunks (Sec. 4.3, dynamic assignment);
+//     inclusive prefix of the list lengths (vc_owner);
+//   * degree-aware workers (Sec. 4.3): d+ < 2 is skipped; 2 <= d+ <= T_w goes
+//     to warp workers, d+ > T_w to thread-block workers whose out-list is split
+//     into work items; both pull work from atomic queues (Sec. 4.3, dynamic
+//     assignment);
 //   * hits are summed per lane, reduced per warp and block, and added to one
 //     uint64 total (Algorithm 1, count +=).
+// All tables live entirely in shared memory (sized from d+(u) so that they
+// always have room), so the paper's global-memory spill region is not needed.
 //
-// Sizing (GB300: up to 227 KiB of shared memory per block). Warp tables:
-// B = clamp(nextpow2(d+), 32, Bmax), L = min(Lmax, table_ints / B); the host
-// checks that B*L > T_w. Block tables: B = nextpow2(part), L = min(Lmax,
-// budget/B - 1) >= 2, where N+(u) is split into parts of at most P_max
-// (largest power of two with 3*P_max <= budget) and every part is probed by
-// the whole 2-hop list: |N+(u) ∩ N+(v)| = sum over parts of |part ∩ N+(v)|.
+// Warp workers: packs. A single small vertex leaves a warp waiting on a chain
+// of dependent global loads (list entry -> out-list -> 2-hop bounds -> 2-hop
+// keys) for little work, so a warp takes a *pack* of up to 32 small vertices:
+// every vertex gets its own table in the warp's shared-memory area, the
+// out-lists of the whole pack are inserted as one flat array, and the 2-hop
+// lists of all the pack's out-edges are probed as one virtual combination,
+// each lane carrying the table of the edge it came from. Bounds of 2-hop
+// lists for chunk c+1 are loaded while chunk c is probed, and every lane
+// issues VC_UNROLL independent 2-hop loads before it probes any of them.
+//
+// Pack table layout. The paper interleaves buckets level-major so that a warp
+// scanning one level reads global memory coalesced. A pack table lives in
+// shared memory, where each lane reads its own bucket, so a bucket is stored
+// whole: 4 slots = 16 bytes, fetched with one vector load and compared
+// without branches. B = max(min_buckets, 2 * nextpow2(d+)) keeps the load
+// factor <= 1/2, so a bucket is rarely full and the overflow chain is rarely
+// walked. The per-bucket lengths are bytes (4 per word; an atomicAdd of
+// 1 << 8*(h%4) on the word claims a slot of bucket h) and live after the
+// slots: a table is 4B + B/4 ints.
+//
+// Thread-block workers keep the paper's level-major layout (element j of
+// bucket i at j*B + i, lengths in a separate array): B = nextpow2(part),
+// L = min(Lmax, budget/B - 1) >= 2 levels, with N+(u) split into parts of at
+// most P_max (largest power of two with 3*P_max <= budget), each probed by the
+// whole 2-hop list: |N+(u) ∩ N+(v)| = sum over parts of |part ∩ N+(v)|.
 #include "tc_internal.h"
 
 namespace tcg {
 
 namespace {
 
+#ifndef VC_UNROLL
+#define VC_UNROLL 4
+#endif
+static_assert(VC_UNROLL >= 1 && VC_UNROLL <= 4, "VC_UNROLL in [1, 4]");
+
+#ifndef PACK_MIN_BLOCKS
+#define PACK_MIN_BLOCKS 4
+#endif
+
+constexpr int STAGE_INTS = 160;  // per warp: 4 x 32 compaction lanes | 32 slot hit counters
+constexpr int EMPTY = -1;        // an unused slot (vertex ids are >= 0)
+constexpr int NOKEY = -2;        // the key of a lane with nothing to probe
+
 __device__ __forceinline__ unsigned lanemask_le(int lane) { return (2u << lane) - 1u; }
 __device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
 
-// Algorithm 1 hashTableConstruction, one key: slot = atomicAdd(len[h], 1);
-// full bucket -> next bucket. len may grow past L (a failed claim also
-// increments it); "len >= L" means full.
-__device__ __forceinline__ void table_insert(int* len, int* tab, int B, int L, int w) {
+__device__ __forceinline__ int warp_incl_scan(int v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Virtual-combination index map (Sec. 4.2). Lists live one per lane with
+// inclusive prefix P and exclusive prefix Pex; `listlane` marks the lanes
+// that hold lists. For the window of flat indices [b, b+32), returns the
+// owner list of index b + lane:
+//   j0 + popc(starts & lanemask_le(lane)) - (bit 0 of starts),
+// j0 = number of lists ending at or before b, bit x of `starts` set iff a
+// list starts at b + x (one REDUX.OR). Valid when no empty list starts
+// strictly inside the window (lists are compacted, or empty only before it).
+__device__ __forceinline__ int vc_owner(int b, int P, int Pex, bool listlane, unsigned le) {
+    const int j0 = __popc(__ballot_sync(FULL, listlane && P <= b));
+    // 1 << x for 0 <= x < 32, else 0 (the clamped funnel shift drops the bit)
+    const unsigned bit = listlane ? __funnelshift_lc(0u, 1u, (unsigned)(Pex - b)) : 0u;
+    const unsigned starts = __reduce_or_sync(FULL, bit);
+    return j0 + __popc(starts & le) - (int)(starts & 1u);
+}
+
+// ---- pack tables (bucket-major, 4 slots, byte lengths) ---------------------
+
+// Algorithm 1 hashTableConstruction, one key: claim a slot of bucket h with
+// an atomic add on its length byte; a full bucket (4 claims) sends the key to
+// the next bucket. sm: shared array; tab/lenw: int offsets of the slots and
+// of the length words; mask = B - 1. Lengths count claims (<= keys <= 255).
+__device__ __forceinline__ void insert_b4(int* sm, int tab, int lenw, int mask, int w) {
+    int h = w & mask;
+    for (int s = 0; s <= mask; ++s) {
+        const int sh = 8 * (h & 3);
+        const unsigned old = atomicAdd(reinterpret_cast<unsigned*>(sm + lenw + (h >> 2)), 1u << sh);
+        const int slot = (old >> sh) & 0xff;
+        if (slot < 4) {
+            sm[tab + 4 * h + slot] = w;
+            return;
+        }
+        h = (h + 1) & mask;
+    }
+}
+
+__device__ __forceinline__ int match4(const int4 q, int w) { return (q.x == w) | (q.y == w) | (q.z == w) | (q.w == w); }
+
+// Algorithm 1 linearSearch continued past a full bucket h0 (slow path).
+__device__ __noinline__ int probe_b4_chain(const int* sm, int tab, int mask, int h0, int w) {
+    int h = (h0 + 1) & mask;
+    for (int s = 0; s < mask; ++s) {
+        const int4 q = *reinterpret_cast<const int4*>(sm + tab + 4 * h);
+        const int hit = match4(q, w);
+        if (hit | (q.w == EMPTY)) return hit;
+        h = (h + 1) & mask;
+    }
+    return 0;
+}
+
+// Probe the 2-hop lists of one chunk of up to 32 out-edges against pack
+// tables. Lane i brings the list N+(v_i) = dag_col[s, s+l) and the table of
+// its edge (tab: int offset of the slots, mask = B-1, slot: pack slot).
+// Empty lists are compacted away (stage: STAGE_INTS ints of smem), the rest
+// are combined virtually and dealt out 32 indices at a time, VC_UNROLL
+// windows per step with all loads of a step issued before its probes. A probe
+// is one 16-byte load and four compares; only a lane whose bucket is full and
+// did not match walks the overflow chain.
+template <bool SLOT_HITS>
+__device__ __forceinline__ uint32_t vc_probe_b4(int s, int l, int tab, int mask, int slot, const int* sm,
+                                                const int32_t* __restrict__ dag_col, int lane, int* stage) {
+    const unsigned nem = __ballot_sync(FULL, l > 0);
+    if (nem == 0) return 0;
+    const int c = __popc(nem);
+    if (l > 0) {
+        const int p = __popc(nem & lanemask_lt(lane));
+        stage[p] = s;
+        stage[32 + p] = l;
+        stage[64 + p] = tab;
+        stage[96 + p] = mask | (slot << 16);
+    }
+    __syncwarp();
+    const bool lst = lane < c;
+    const int cs = lst ? stage[lane] : 0;
+    const int cl = lst ? stage[32 + lane] : 0;
+    const int ctab = stage[64 + (lst ? lane : 0)];  // lanes past the lists alias list 0's table
+    const int cms = lst ? stage[96 + lane] : 0;
+    __syncwarp();
+    const int P = warp_incl_scan(cl, lane);
+    const int total = __shfl_sync(FULL, P, 31);
+    const int Pex = P - cl;
+    const int bias = cs - Pex;  // dag_col index of flat position f of this list: bias + f
+    const unsigned le = lanemask_le(lane);
+    uint32_t hits = 0;
+    for (int base = 0; base < total; base += 32 * VC_UNROLL) {
+        int key[VC_UNROLL], kt[VC_UNROLL], km[VC_UNROLL];
+#pragma unroll
+        for (int q = 0; q < VC_UNROLL; ++q) {
+            const int b = base + 32 * q;
+            const int o = vc_owner(b, P, Pex, lst, le) & 31;
+            const int bo = __shfl_sync(FULL, bias, o);
+            kt[q] = __shfl_sync(FULL, ctab, o);
+            km[q] = __shfl_sync(FULL, cms, o);
+            const int f = b + lane;
+            key[q] = (f < total) ? __ldg(dag_col + bo + f) : NOKEY;
+        }
+#pragma unroll
+        for (int q = 0; q < VC_UNROLL; ++q) {
+            const int mask = km[q] & 0xffff;
+            const int h = key[q] & mask;
+            const int4 b4 = *reinterpret_cast<const int4*>(sm + kt[q] + 4 * h);
+            int hit = match4(b4, key[q]);
+            const bool more = key[q] >= 0 && !hit && b4.w != EMPTY;
+            if (__any_sync(FULL, more)) {
+                if (more) hit = probe_b4_chain(sm, kt[q], mask, h, key[q]);
+            }
+            hits += hit;
+            if (SLOT_HITS && hit) atomicAdd(&stage[128 + (km[q] >> 16)], 1);
+        }
+    }
+    return hits;
+}
+
+// ---- thread-block tables (level-major, L levels) ----------------------------
+
+// Algorithm 1 hashTableConstruction, one key. len[h] starts at EMPTY (-1),
+// so atomicAdd(len[h], 1) + 1 is the claimed level; a full bucket (level >=
+// L) sends the key to the next bucket. Levels never written stay EMPTY, so a
+// search stops at the first empty level without reading len.
+__device__ __forceinline__ void insert_lm(int* len, int* tab, int B, int L, int w) {
     int h = w & (B - 1);
     for (int s = 0; s < B; ++s) {
-        const int slot = atomicAdd(&len[h], 1);
+        const int slot = atomicAdd(&len[h], 1) + 1;
         if (slot < L) {
             tab[slot * B + h] = w;
             return;
@@ -56,44 +212,25 @@ __device__ __forceinline__ void table_insert(int* len, int* tab, int B, int L, i
     }
 }
 
-// Algorithm 1 linearSearch over the bucket of w and, while the scanned bucket
-// was full, its successors.
-__device__ __forceinline__ int table_probe(const int* len, const int* tab, int B, int L, int w) {
+// Algorithm 1 linearSearch over the levels of bucket hash(w), then of its
+// successors while the scanned bucket was full.
+__device__ __forceinline__ int probe_lm(const int* tab, int B, int L, int w) {
     int h = w & (B - 1);
     for (int s = 0; s < B; ++s) {
-        const int ln = len[h];
-        const int c = ln < L ? ln : L;
-        for (int j = 0; j < c; ++j)
-            if (tab[j * B + h] == w) return 1;
-        if (ln < L) return 0;
+        for (int j = 0; j < L; ++j) {
+            const int x = tab[j * B + h];
+            if (x == w) return 1;
+            if (x == EMPTY) return 0;
+        }
         h = (h + 1) & (B - 1);
     }
     return 0;
 }
 
-// Virtual combination over the 2-hop lists of up to 32 out-neighbours
-// nbrs[0..cnt): lane j loads neighbour j and its list bounds; the non-empty
-// lists are compacted to lanes 0..c-1 and scanned; then the flat index range
-// [0, total) is dealt to the lanes 32 at a time. For a window starting at
-// `base`, the owner of lane L's index is
-//   j0 + popc(starts & lanemask_le(L)) - (bit 0 of starts)
-// where j0 = number of lists ending at or before base and `starts` has bit x
-// set iff a list starts at base + x (one REDUX.OR). stage: 64 ints of smem.
-__device__ __forceinline__ uint32_t warp_probe_chunk(const int32_t* __restrict__ nbrs, int cnt,
-                                                     const int32_t* __restrict__ dag_ptr,
-                                                     const int32_t* __restrict__ dag_col, const int* len,
-                                                     const int* tab, int B, int L, int lane, int* stage,
-                                                     int n, DevCounters* ctr) {
-    int s = 0, l = 0;
-    if (lane < cnt) {
-        const int v = nbrs[lane];
-        if ((unsigned)v < (unsigned)n) {
-            s = dag_ptr[v];
-            l = dag_ptr[v + 1] - s;
-        } else {
-            atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
-        }
-    }
+// Same virtual combination as vc_probe_b4, all lists probed against one
+// level-major table.
+__device__ __forceinline__ uint32_t vc_probe_lm(int s, int l, const int* tab, int B, int L,
+                                                const int32_t* __restrict__ dag_col, int lane, int* stage) {
     const unsigned nem = __ballot_sync(FULL, l > 0);
     if (nem == 0) return 0;
     const int c = __popc(nem);
@@ -103,32 +240,34 @@ __device__ __forceinline__ uint32_t warp_probe_chunk(const int32_t* __restrict__
         stage[32 + p] = l;
     }
     __syncwarp();
-    const int cs = (lane < c) ? stage[lane] : 0;
-    const int cl = (lane < c) ? stage[32 + lane] : 0;
+    const bool lst = lane < c;
+    const int cs = lst ? stage[lane] : 0;
+    const int cl = lst ? stage[32 + lane] : 0;
     __syncwarp();
-    int P = cl;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(FULL, P, o);
-        if (lane >= o) P += t;
-    }
+    const int P = warp_incl_scan(cl, lane);
     const int total = __shfl_sync(FULL, P, 31);
     const int Pex = P - cl;
+    const int bias = cs - Pex;
     const unsigned le = lanemask_le(lane);
     uint32_t hits = 0;
-    for (int base = 0; base < total; base += 32) {
-        const int j0 = __popc(__ballot_sync(FULL, lane < c && P <= base));
-        const int x = Pex - base;
-        const unsigned bit = (lane < c && x >= 0 && x < 32) ? (1u << x) : 0u;
-        const unsigned starts = __reduce_or_sync(FULL, bit);
-        const int o = j0 + __popc(starts & le) - (int)(starts & 1u);
-        const int so = __shfl_sync(FULL, cs, o & 31);
-        const int po = __shfl_sync(FULL, Pex, o & 31);
-        const int f = base + lane;
-        if (f < total) hits += table_probe(len, tab, B, L, dag_col[so + (f - po)]);
+    for (int base = 0; base < total; base += 32 * VC_UNROLL) {
+        int key[VC_UNROLL];
+#pragma unroll
+        for (int q = 0; q < VC_UNROLL; ++q) {
+            const int b = base + 32 * q;
+            const int o = vc_owner(b, P, Pex, lst, le) & 31;
+            const int bo = __shfl_sync(FULL, bias, o);
+            const int f = b + lane;
+            key[q] = (f < total) ? __ldg(dag_col + bo + f) : NOKEY;
+        }
+#pragma unroll
+        for (int q = 0; q < VC_UNROLL; ++q)
+            if (key[q] >= 0) hits += probe_lm(tab, B, L, key[q]);
     }
     return hits;
 }
+
+// ---- workers -----------------------------------------------------------------
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
@@ -149,65 +288,150 @@ __device__ __forceinline__ void block_add_total(unsigned long long acc, DevCount
     }
 }
 
-// Warp workers: one warp per vertex with 2 <= d+ <= T_w, warp-private table.
-// smem per warp: len[Bmax] | tab[table_ints] | stage[64].
-__global__ void __launch_bounds__(256)
-    k_count_warp(const int32_t* __restrict__ dag_ptr, const int32_t* __restrict__ dag_col,
-                 const int32_t* __restrict__ warp_list, unsigned long long* __restrict__ per_vertex,
-                 DevCounters* ctr, int n, int table_ints, int max_buckets, int max_levels, int chunk) {
+// Bounds of N+(v) for an out-neighbour v (0/0 for no neighbour or a bad id).
+__device__ __forceinline__ void list_bounds(int v, const int32_t* __restrict__ dag_ptr, int n, DevCounters* ctr,
+                                            int& s, int& l) {
+    s = 0;
+    l = 0;
+    if (v >= 0) {
+        if (v < n) {
+            s = __ldg(dag_ptr + v);
+            l = __ldg(dag_ptr + v + 1) - s;
+        } else {
+            atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
+        }
+    }
+}
+
+// Warp workers over packs of small vertices (2 <= d+ <= T_w).
+// smem per warp: area[area_ints] | stage[STAGE_INTS]. desc[i] = (first
+// out-edge, d+) of warp_list[i]. A pack's area holds all its tables' slots
+// first, then all their length words.
+template <bool PER_VERTEX>
+__global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
+    k_count_pack(const int32_t* __restrict__ dag_ptr, const int32_t* __restrict__ dag_col,
+                 const int2* __restrict__ desc, const int32_t* __restrict__ warp_list,
+                 unsigned long long* __restrict__ per_vertex, DevCounters* ctr, int n, int area_ints,
+                 int lg_min_buckets, int pop) {
     extern __shared__ int smem[];
     if (ctr->err) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int* len = smem + w * (max_buckets + table_ints + 64);
-    int* tab = len + max_buckets;
-    int* stage = tab + table_ints;
+    const unsigned le = lanemask_le(lane);
+    const int area = w * (area_ints + STAGE_INTS);  // int offset of this warp's area in smem
+    int* stage = smem + area + area_ints;
     const int nlist = ctr->n_warp;
     unsigned long long acc = 0;
     for (;;) {
         int i0 = 0;
-        if (lane == 0) i0 = atomicAdd(&ctr->q_warp, chunk);
+        if (lane == 0) i0 = atomicAdd(&ctr->q_warp, pop);
         i0 = __shfl_sync(FULL, i0, 0);
         if (i0 >= nlist) break;
-        const int i1 = min(i0 + chunk, nlist);
-        for (int i = i0; i < i1; ++i) {
-            const int u = warp_list[i];
-            const int a = dag_ptr[u];
-            const int k = dag_ptr[u + 1] - a;
-            int B = next_pow2(k);
-            B = B < 32 ? 32 : (B > max_buckets ? max_buckets : B);
-            int L = table_ints / B;
-            L = L < max_levels ? L : max_levels;
-            for (int t = lane; t < B; t += 32) len[t] = 0;
+        const int cnt = min(pop, nlist - i0);
+        int a = 0, k = 0;
+        if (lane < cnt) {
+            const int2 d = __ldg(desc + i0 + lane);
+            a = d.x;
+            k = d.y;
+        }
+        int lgB = 33 - __clz(k > 1 ? k - 1 : 1);  // log2(2 * nextpow2(k))
+        lgB = lgB < lg_min_buckets ? lg_min_buckets : lgB;
+        const int B = 1 << lgB;
+        const int ftab = (lane < cnt) ? 4 * B : 0, flen = (lane < cnt) ? B / 4 : 0;
+        for (int p0 = 0; p0 < cnt;) {
+            // the pack: the longest run of vertices from p0 whose tables fit the area
+            const int ft = lane >= p0 ? ftab : 0, fl = lane >= p0 ? flen : 0;
+            const int FT = warp_incl_scan(ft, lane), FL = warp_incl_scan(fl, lane);
+            const bool take = lane >= p0 && lane < cnt && (FT + FL <= area_ints || lane == p0);
+            const int p1 = p0 + __popc(__ballot_sync(FULL, take));
+            const bool in = lane >= p0 && lane < p1;
+            const int tab_used = __shfl_sync(FULL, FT, p1 - 1), len_used = __shfl_sync(FULL, FL, p1 - 1);
+            const int my_tab = area + FT - ft;                  // slots of this lane's table
+            const int my_len = area + tab_used + FL - fl;       // its length words
+            for (int t = lane * 4; t < tab_used; t += 128)
+                *reinterpret_cast<int4*>(smem + area + t) = make_int4(EMPTY, EMPTY, EMPTY, EMPTY);
+            for (int t = lane * 4; t < len_used; t += 128)
+                *reinterpret_cast<int4*>(smem + area + tab_used + t) = make_int4(0, 0, 0, 0);
+            if (PER_VERTEX) stage[128 + lane] = 0;
             __syncwarp();
-            for (int t = lane; t < k; t += 32) table_insert(len, tab, B, L, dag_col[a + t]);
-            __syncwarp();
-            uint32_t h = 0;
-            for (int c0 = 0; c0 < k; c0 += 32)
-                h += warp_probe_chunk(dag_col + a + c0, min(32, k - c0), dag_ptr, dag_col, len, tab, B, L, lane,
-                                      stage, n, ctr);
-            acc += h;
-            if (per_vertex) {
-                const unsigned long long hu = warp_sum_u64(h);
-                if (lane == 0) per_vertex[u] = hu;
+            // build every table of the pack from the pack's out-lists, one flat array
+            const int kk = in ? k : 0;
+            const int K = warp_incl_scan(kk, lane);
+            const int Kex = K - kk;
+            const int kbias = a - Kex;  // dag_col index of flat out-edge e owned by this lane
+            const int E = __shfl_sync(FULL, K, 31);
+            for (int b0 = 0; b0 < E; b0 += 32 * VC_UNROLL) {
+                int key[VC_UNROLL], own[VC_UNROLL];
+#pragma unroll
+                for (int q = 0; q < VC_UNROLL; ++q) {
+                    const int b = b0 + 32 * q;
+                    const int o = vc_owner(b, K, Kex, true, le) & 31;
+                    const int bo = __shfl_sync(FULL, kbias, o);
+                    own[q] = o;
+                    key[q] = (b + lane < E) ? __ldg(dag_col + bo + b + lane) : NOKEY;
+                }
+#pragma unroll
+                for (int q = 0; q < VC_UNROLL; ++q) {
+                    const int tb = __shfl_sync(FULL, my_tab, own[q]);
+                    const int lw = __shfl_sync(FULL, my_len, own[q]);
+                    const int mk = __shfl_sync(FULL, B, own[q]) - 1;
+                    if (key[q] >= 0) insert_b4(smem, tb, lw, mk, key[q]);
+                }
             }
             __syncwarp();
+            // probe: chunks of 32 out-edges, bounds of the next chunk prefetched
+            uint32_t hits = 0;
+            int s = 0, l = 0, etab = 0, emask = 0, eslot = 0;
+            {
+                const int o = vc_owner(0, K, Kex, true, le) & 31;
+                const int bo = __shfl_sync(FULL, kbias, o);
+                etab = __shfl_sync(FULL, my_tab, o);
+                emask = __shfl_sync(FULL, B, o) - 1;
+                eslot = o;
+                list_bounds(lane < E ? __ldg(dag_col + bo + lane) : -1, dag_ptr, n, ctr, s, l);
+            }
+            for (int c0 = 0; c0 < E; c0 += 32) {
+                int ns = 0, nl = 0, ntab = 0, nmask = 0, nslot = 0;
+                if (c0 + 32 < E) {
+                    const int o = vc_owner(c0 + 32, K, Kex, true, le) & 31;
+                    const int bo = __shfl_sync(FULL, kbias, o);
+                    ntab = __shfl_sync(FULL, my_tab, o);
+                    nmask = __shfl_sync(FULL, B, o) - 1;
+                    nslot = o;
+                    const int e = c0 + 32 + lane;
+                    list_bounds(e < E ? __ldg(dag_col + bo + e) : -1, dag_ptr, n, ctr, ns, nl);
+                }
+                hits += vc_probe_b4<PER_VERTEX>(s, l, etab, emask, eslot, smem, dag_col, lane, stage);
+                s = ns;
+                l = nl;
+                etab = ntab;
+                emask = nmask;
+                eslot = nslot;
+            }
+            acc += hits;
+            if (PER_VERTEX) {
+                __syncwarp();
+                if (in) per_vertex[__ldg(warp_list + i0 + lane)] = (unsigned long long)stage[128 + lane];
+            }
+            __syncwarp();
+            p0 = p1;
         }
     }
     block_add_total(acc, ctr);
 }
 
 // Thread-block workers: one block per work item (u, first neighbour) of a
-// vertex with d+ > T_w. smem: stage[nwarps*64] | len[B] | tab[B*L].
-__global__ void __launch_bounds__(1024)
+// vertex with d+ > T_w. smem: stage[nwarps * STAGE_INTS] | len[B] | tab[B*L].
+// Warp w of the block takes the item's 32-neighbour chunks w, w + nw, ...
+__global__ void __launch_bounds__(1024, 1)
     k_count_block(const int32_t* __restrict__ dag_ptr, const int32_t* __restrict__ dag_col,
                   const int2* __restrict__ items, unsigned long long* __restrict__ per_vertex, DevCounters* ctr,
                   int n, int budget_ints, int part_max, int max_levels, int item_nbrs) {
     extern __shared__ int smem[];
-    __shared__ int s_item, s_next;
+    __shared__ int s_item;
     if (ctr->err) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int* stage = smem + w * 64;
-    int* len = smem + nw * 64;
+    int* stage = smem + w * STAGE_INTS;
+    int* area = smem + nw * STAGE_INTS;
     const int nitems = ctr->n_items;
     unsigned long long acc = 0;
     for (;;) {
@@ -227,19 +451,22 @@ __global__ void __launch_bounds__(1024)
             const int B = next_pow2(pk < 32 ? 32 : pk);
             int L = budget_ints / B - 1;
             L = L < max_levels ? L : max_levels;
-            int* tab = len + B;
-            for (int t = threadIdx.x; t < B; t += blockDim.x) len[t] = 0;
-            if (threadIdx.x == 0) s_next = nb0;
+            for (int t = threadIdx.x; t < B * (L + 1); t += blockDim.x) area[t] = EMPTY;
             __syncthreads();
-            for (int t = threadIdx.x; t < pk; t += blockDim.x) table_insert(len, tab, B, L, dag_col[a + p0 + t]);
+            for (int t = threadIdx.x; t < pk; t += blockDim.x)
+                insert_lm(area, area + B, B, L, __ldg(dag_col + a + p0 + t));
             __syncthreads();
-            for (;;) {
-                int c0 = 0;
-                if (lane == 0) c0 = atomicAdd(&s_next, 32);
-                c0 = __shfl_sync(FULL, c0, 0);
-                if (c0 >= nb1) break;
-                h += warp_probe_chunk(dag_col + a + c0, min(32, nb1 - c0), dag_ptr, dag_col, len, tab, B, L, lane,
-                                      stage, n, ctr);
+            int c0 = nb0 + 32 * w;
+            int s = 0, l = 0;
+            if (c0 < nb1) list_bounds(c0 + lane < nb1 ? __ldg(dag_col + a + c0 + lane) : -1, dag_ptr, n, ctr, s, l);
+            for (; c0 < nb1; c0 += 32 * nw) {
+                const int c1 = c0 + 32 * nw;
+                int ns = 0, nl = 0;
+                if (c1 < nb1)
+                    list_bounds(c1 + lane < nb1 ? __ldg(dag_col + a + c1 + lane) : -1, dag_ptr, n, ctr, ns, nl);
+                h += vc_probe_lm(s, l, area + B, B, L, dag_col, lane, stage);
+                s = ns;
+                l = nl;
             }
             __syncthreads();
         }
@@ -301,16 +528,42 @@ __global__ void k_stats(const int32_t* __restrict__ dag_ptr, const int32_t* __re
     }
 }
 
+int pack_smem_bytes(const CountCfg& cfg) { return cfg.warps_per_block * (cfg.warp_area_ints + STAGE_INTS) * 4; }
+
+using PackKernel = void (*)(const int32_t*, const int32_t*, const int2*, const int32_t*, unsigned long long*,
+                            DevCounters*, int, int, int, int);
+
+PackKernel pack_kernel(bool per_vertex) { return per_vertex ? k_count_pack<true> : k_count_pack<false>; }
+
+int lg2(int x) {
+    int l = 0;
+    while ((1 << l) < x) ++l;
+    return l;
+}
+
 }  // namespace
 
+int pack_table_ints(int max_out_degree, int min_buckets) {
+    int b = 2 * next_pow2(max_out_degree < 1 ? 1 : max_out_degree);
+    if (b < min_buckets) b = min_buckets;
+    return 4 * b + b / 4;
+}
+
+int count_block_budget_ints(const CountCfg& cfg) {
+    return cfg.block_smem_bytes / 4 - (cfg.block_threads / 32) * STAGE_INTS;
+}
+
 cudaError_t count_kernel_setup(CountCfg& cfg, int num_sms) {
-    const int warp_smem = cfg.warps_per_block * (cfg.warp_max_buckets + cfg.warp_table_ints + 64) * 4;
-    cudaError_t e = cudaFuncSetAttribute(k_count_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem);
+    const int warp_smem = pack_smem_bytes(cfg);
+    cudaError_t e = cudaSuccess;
+    for (int pv = 0; pv < 2 && e == cudaSuccess; ++pv)
+        e = cudaFuncSetAttribute(pack_kernel(pv), cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_count_block, cudaFuncAttributeMaxDynamicSharedMemorySize, cfg.block_smem_bytes);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_warp, cfg.warps_per_block * 32, warp_smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pack_kernel(false), cfg.warps_per_block * 32,
+                                                      warp_smem);
     if (e != cudaSuccess) return e;
     cfg.warp_grid = num_sms * (per_sm > 0 ? per_sm : 1);
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_block, cfg.block_threads, cfg.block_smem_bytes);
@@ -320,18 +573,16 @@ cudaError_t count_kernel_setup(CountCfg& cfg, int num_sms) {
 }
 
 cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t n, const int32_t* warp_list,
-                         const int2* items, unsigned long long* per_vertex, const CountCfg& cfg, DevCounters* ctr,
-                         cudaStream_t st) {
-    const int nwb = cfg.block_threads / 32;
-    const int budget = cfg.block_smem_bytes / 4 - nwb * 64;
+                         const int2* warp_desc, const int2* items, unsigned long long* per_vertex,
+                         const CountCfg& cfg, DevCounters* ctr, cudaStream_t st) {
+    const int budget = count_block_budget_ints(cfg);
     int part_max = 1;
     while (part_max * 2 * 3 <= budget) part_max *= 2;
     k_count_block<<<cfg.block_grid, cfg.block_threads, cfg.block_smem_bytes, st>>>(
         dag_ptr, dag_col, items, per_vertex, ctr, (int)n, budget, part_max, cfg.max_levels, cfg.item_neighbors);
-    const int warp_smem = cfg.warps_per_block * (cfg.warp_max_buckets + cfg.warp_table_ints + 64) * 4;
-    k_count_warp<<<cfg.warp_grid, cfg.warps_per_block * 32, warp_smem, st>>>(
-        dag_ptr, dag_col, warp_list, per_vertex, ctr, (int)n, cfg.warp_table_ints, cfg.warp_max_buckets,
-        cfg.max_levels, cfg.chunk);
+    pack_kernel(per_vertex != nullptr)<<<cfg.warp_grid, cfg.warps_per_block * 32, pack_smem_bytes(cfg), st>>>(
+        dag_ptr, dag_col, warp_desc, warp_list, per_vertex, ctr, (int)n, cfg.warp_area_ints,
+        lg2(cfg.warp_min_buckets), cfg.chunk);
     return cudaGetLastError();
 }
 

@@ -45,6 +45,7 @@ __global__ void k_degree(const Off* __restrict__ row_ptr, int64_t n, int64_t nnz
 
 constexpr int ORIENT_THREADS = 256;
 constexpr int ORIENT_WARPS = ORIENT_THREADS / 32;
+constexpr int ORIENT_UNROLL = 4;
 
 // COMPACT == false: kept[u] = out-degree. COMPACT == true: write dag_col.
 template <typename Off, bool COMPACT>
@@ -83,44 +84,58 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
         __syncwarp();
         const long long gb = __shfl_sync(FULL, a, 0), ge = e;
         int r = 0;
-        for (long long base = gb; base < ge; base += 32) {
-            const long long f = base + lane;
-            const bool act = f < ge;
-            bool keep = false;
-            int v = 0;
-            if (act) {
-                while (st[r + 1] <= f) ++r;
-                v = col[f];
-                if ((unsigned)v >= (unsigned long long)n) {
-                    atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
-                } else {
-                    const int du = (int)(st[r + 1] - st[r]);
-                    const int dv = deg[v];
-                    keep = (dv > du) || (dv == du && (int64_t)v > u0 + r);
+        for (long long base = gb; base < ge; base += 32 * ORIENT_UNROLL) {
+            // issue every load of the step first: ORIENT_UNROLL col reads, then
+            // their degree gathers, so each lane has that many requests in flight
+            int vq[ORIENT_UNROLL], dq[ORIENT_UNROLL];
+#pragma unroll
+            for (int q = 0; q < ORIENT_UNROLL; ++q) {
+                const long long f = base + 32 * q + lane;
+                vq[q] = (f < ge) ? __ldg(col + f) : -1;
+            }
+#pragma unroll
+            for (int q = 0; q < ORIENT_UNROLL; ++q)
+                dq[q] = ((unsigned)vq[q] < (unsigned long long)n) ? __ldg(deg + vq[q]) : 0;
+#pragma unroll
+            for (int q = 0; q < ORIENT_UNROLL; ++q) {
+                const long long f = base + 32 * q + lane;
+                const bool act = f < ge;
+                bool keep = false;
+                const int v = vq[q];
+                if (act) {
+                    while (st[r + 1] <= f) ++r;
+                    if ((unsigned)v >= (unsigned long long)n) {
+                        atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
+                    } else {
+                        const int du = (int)(st[r + 1] - st[r]);
+                        const int dv = dq[q];
+                        keep = (dv > du) || (dv == du && (int64_t)v > u0 + r);
+                    }
                 }
+                const unsigned km = __ballot_sync(FULL, keep);
+                const unsigned am = __ballot_sync(FULL, act);
+                if (am == 0) break;
+                const int rp = __shfl_up_sync(FULL, r, 1);
+                const int rn = __shfl_down_sync(FULL, r, 1);
+                const bool seg_start = act && (lane == 0 || rp != r);
+                const bool seg_end = act && (lane == 31 || !((am >> (lane + 1)) & 1u) || rn != r);
+                const unsigned sm = __ballot_sync(FULL, seg_start);
+                unsigned segbits = 0;
+                if (act) {
+                    const int first = 31 - __clz(sm & le);
+                    segbits = ~((1u << first) - 1u);
+                }
+                if (COMPACT && keep) {
+                    const long long pos = (long long)dp[r] + cnt[r] + __popc(km & lt & segbits);
+                    if (pos < dag_cap)
+                        dag_col[pos] = v;
+                    else
+                        atomicOr(&ctr->err, ERRBIT_DAG_OVERFLOW);
+                }
+                __syncwarp();
+                if (seg_end) cnt[r] += __popc(km & le & segbits);
+                __syncwarp();
             }
-            const unsigned km = __ballot_sync(FULL, keep);
-            const unsigned am = __ballot_sync(FULL, act);
-            const int rp = __shfl_up_sync(FULL, r, 1);
-            const int rn = __shfl_down_sync(FULL, r, 1);
-            const bool seg_start = act && (lane == 0 || rp != r);
-            const bool seg_end = act && (lane == 31 || !((am >> (lane + 1)) & 1u) || rn != r);
-            const unsigned sm = __ballot_sync(FULL, seg_start);
-            unsigned segbits = 0;
-            if (act) {
-                const int first = 31 - __clz(sm & le);
-                segbits = ~((1u << first) - 1u);
-            }
-            if (COMPACT && keep) {
-                const long long pos = (long long)dp[r] + cnt[r] + __popc(km & lt & segbits);
-                if (pos < dag_cap)
-                    dag_col[pos] = v;
-                else
-                    atomicOr(&ctr->err, ERRBIT_DAG_OVERFLOW);
-            }
-            __syncwarp();
-            if (seg_end) cnt[r] += __popc(km & le & segbits);
-            __syncwarp();
         }
         if (!COMPACT && lane < nr) kept[u0 + lane] = cnt[lane];
         __syncwarp();
@@ -230,15 +245,18 @@ __global__ void __launch_bounds__(SCAN_THREADS)
 // ---- binning ----------------------------------------------------------------
 
 __global__ void k_bin(const int32_t* __restrict__ dag_ptr, int64_t n, int warp_max, int item_nbrs, int shard_count,
-                      int shard_index, int32_t* __restrict__ warp_list, int2* __restrict__ items, int64_t item_cap,
-                      DevCounters* ctr) {
+                      int shard_index, int32_t* __restrict__ warp_list, int2* __restrict__ warp_desc,
+                      int2* __restrict__ items, int64_t item_cap, DevCounters* ctr) {
     if (ctr->err) return;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
         const int64_t u = base + threadIdx.x;
-        int d = 0;
-        if (u < n && (shard_count <= 1 || (int)(u % shard_count) == shard_index)) d = dag_ptr[u + 1] - dag_ptr[u];
+        int d = 0, a = 0;
+        if (u < n && (shard_count <= 1 || (int)(u % shard_count) == shard_index)) {
+            a = dag_ptr[u];
+            d = dag_ptr[u + 1] - a;
+        }
         const bool is_warp = d >= 2 && d <= warp_max;
         const unsigned wm = __ballot_sync(FULL, is_warp);
         if (wm) {
@@ -246,7 +264,11 @@ __global__ void k_bin(const int32_t* __restrict__ dag_ptr, int64_t n, int warp_m
             int pos = 0;
             if (lane == leader) pos = atomicAdd(&ctr->n_warp, __popc(wm));
             pos = __shfl_sync(FULL, pos, leader);
-            if (is_warp) warp_list[pos + __popc(wm & lanemask_lt(lane))] = (int32_t)u;
+            if (is_warp) {
+                const int at = pos + __popc(wm & lanemask_lt(lane));
+                warp_list[at] = (int32_t)u;
+                warp_desc[at] = make_int2(a, d);
+            }
         }
         if (d > warp_max) {
             const int k = (d + item_nbrs - 1) / item_nbrs;
@@ -297,13 +319,13 @@ cudaError_t launch_orient(const void* row_ptr, int offset_bits, const int32_t* c
                     ctr, num_sms, st);
 }
 
-cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* items,
-                       int64_t item_cap, DevCounters* ctr, int num_sms, cudaStream_t st) {
+cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* warp_desc,
+                       int2* items, int64_t item_cap, DevCounters* ctr, int num_sms, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     int g = (int)((n + 255) / 256);
     if (g > num_sms * 16) g = num_sms * 16;
     k_bin<<<g, 256, 0, st>>>(dag_ptr, n, cfg.warp_max_out_degree, cfg.item_neighbors, cfg.shard_count,
-                             cfg.shard_index, warp_list, items, item_cap, ctr);
+                             cfg.shard_index, warp_list, warp_desc, items, item_cap, ctr);
     return cudaGetLastError();
 }
 

@@ -35,9 +35,9 @@ static_assert(sizeof(DevCounters) == 64, "DevCounters layout");
 // Resolved launch parameters (host fills from tc_params + device properties).
 struct CountCfg {
     int warp_max_out_degree;   // T_w
-    int warp_table_ints;       // per-warp table capacity
-    int warp_max_buckets;      // power of two
-    int max_levels;            // L cap
+    int warp_area_ints;        // per-warp table area
+    int warp_min_buckets;      // power of two
+    int max_levels;            // L cap of block tables
     int warps_per_block;       // warp kernel
     int warp_grid;             // persistent grid of the warp kernel
     int block_threads;         // block kernel
@@ -50,20 +50,23 @@ struct CountCfg {
 
 // ---- orientation (orient.cu) ----------------------------------------------
 // deg, kept: int32[n]; partial: int64[scan_blocks(n)+1]; dag_ptr: int32[n+1];
-// warp_list: int32[n]; items: int2[item_cap].
+// warp_list: int32[n]; warp_desc: int2[n]; items: int2[item_cap].
 int scan_blocks(int64_t n);
 cudaError_t launch_orient(const void* row_ptr, int offset_bits, const int32_t* col, int64_t n, int64_t nnz,
                           int32_t* deg, int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
                           int64_t dag_cap, DevCounters* ctr, int num_sms, cudaStream_t st);
 
 // Binning (Sec. 4.3) from an existing DAG: fills warp_list / items / counters.
-cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* items,
-                       int64_t item_cap, DevCounters* ctr, int num_sms, cudaStream_t st);
+cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* warp_desc,
+                       int2* items, int64_t item_cap, DevCounters* ctr, int num_sms, cudaStream_t st);
 
 // ---- counting (count.cu) ----------------------------------------------------
 cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t n, const int32_t* warp_list,
-                         const int2* items, unsigned long long* per_vertex, const CountCfg& cfg, DevCounters* ctr,
-                         cudaStream_t st);
+                         const int2* warp_desc, const int2* items, unsigned long long* per_vertex,
+                         const CountCfg& cfg, DevCounters* ctr, cudaStream_t st);
+int count_block_budget_ints(const CountCfg& cfg);
+// ints of one warp-worker table for out-degree d (2*nextpow2(d) buckets of 4 slots + byte lengths)
+int pack_table_ints(int max_out_degree, int min_buckets);
 cudaError_t count_kernel_setup(CountCfg& cfg, int num_sms);
 cudaError_t launch_finish(const DevCounters* ctr, unsigned long long* count_out, int* err_out, cudaStream_t st);
 

@@ -158,12 +158,15 @@ def test_per_vertex_counts(ctx):
 # ------------------------------------------------------ worker/table regimes
 
 PARAM_SETS = {
-    "tiny_levels": dict(max_levels=2),                         # overflow chains everywhere
+    "tiny_levels": dict(max_levels=2),                         # block-table overflow chains everywhere
+    "one_table_per_pack": dict(warp_max_out_degree=12, warp_area_ints=136),
     "all_block": dict(warp_max_out_degree=1),                  # every vertex on the block path
-    "all_warp": dict(warp_max_out_degree=2000, warp_table_ints=4096, warp_max_buckets=1024, warps_per_block=4),
+    "all_warp": dict(warp_max_out_degree=255, warp_area_ints=2176, warps_per_block=4),
+    "one_per_pop": dict(chunk=1),
+    "big_min_buckets": dict(warp_min_buckets=512, warp_area_ints=2176),
     "small_items": dict(item_neighbors=32, warp_max_out_degree=16),
     "split_parts": dict(block_threads=64, block_smem_bytes=4096, warp_max_out_degree=8),  # part_max = 256
-    "chunk7": dict(chunk=7),
+    "chunk7": dict(chunk=7, warp_area_ints=4608),
 }
 
 
@@ -184,7 +187,7 @@ def _bucket_collision_graph(k, stride=1024):
     return G.from_edge_list(n, e)
 
 
-@pytest.mark.parametrize("k,params", [(60, {}), (300, {}), (60, dict(max_levels=3)),
+@pytest.mark.parametrize("k,params", [(60, {}), (300, {}), (200, dict(warp_max_out_degree=255, warp_area_ints=2176)),
                                       (300, dict(max_levels=2)), (500, dict(block_threads=64,
                                                                             block_smem_bytes=4096))])
 def test_adversarial_overflow(T, k, params):
@@ -272,8 +275,9 @@ def test_asymmetric_input_does_not_overflow(T, ctx):
 
 
 def test_invalid_params(T):
-    for bad in (dict(warp_max_buckets=48), dict(max_levels=1), dict(shard_count=2, shard_index=2),
-                dict(warp_max_out_degree=5000), dict(block_threads=100)):
+    for bad in (dict(warp_min_buckets=48), dict(max_levels=1), dict(shard_count=2, shard_index=2),
+                dict(warp_max_out_degree=256), dict(block_threads=100), dict(chunk=33), dict(warp_area_ints=320),
+                dict(warp_min_buckets=8)):
         with pytest.raises(T.TcError) as ei:
             T.Context(0, params=bad)
         assert ei.value.status == T.TC_ERR_INVALID_ARG
