@@ -1,0 +1,348 @@
+#!/usr/bin/env python3
+"""Benchmark of the hot path: rank-by-degree orientation + vertex-centric
+hashed triangle counting, on the random-geometric-graph workload (2^22 points
+uniform in the unit square, radius set for mean degree 64, seed 2).
+
+One step = one tc_count_async over the device-resident CSR: degree,
+orientation counts, scan, compaction, binning, hash build + probe, 64-bit
+reduction. Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+With N > 1 (torchrun) every rank holds the whole CSR and counts the
+vertices u with u % N == rank (the workload partition of Sec. 5.1); the
+per-rank counts are summed once, after timing. The reference arm times the
+CPU oracle on the host cores (a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="rgg-2^22-meandeg64-seed2", points_log2=22, mean_degree=64.0, seed=2)
+REF_SAMPLE = dict(name="rgg-2^20-meandeg64-seed2", points_log2=20, mean_degree=64.0, seed=2)
+METRIC = "triangle-count TEPS"
+UNIT = "edges/s"
+FALLBACK_HBM_GBS = 6800.0
+PROFILE = os.path.join(ROOT, "profiles", "k_count_pack__rgg22.md")
+COUNT_SRC = os.path.join(ROOT, "paper_2103_08053_gb300", "csrc", "count.cu")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def make_graph(spec):
+    import graphgen as G
+    return G.rgg(1 << spec["points_log2"], spec["mean_degree"], seed=spec["seed"])
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- roofline
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        v = float(json.load(open(p))["hbm_gbs"])
+        return v, "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def count_source_hash() -> str:
+    return hashlib.sha256(open(COUNT_SRC, "rb").read()).hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the counting kernel from the committed ncu
+    summary, or None when the kernel source changed since the capture."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    h = re.search(r"count\.cu sha256\[:16\]:\s*([0-9a-f]{16})", text)
+    b = re.search(r"dram bytes per launch \(read\+write\):\s*([0-9.eE+]+)", text)
+    if not h or not b or h.group(1) != count_source_hash():
+        return None
+    return float(b.group(1))
+
+
+def count_phase_bytes(n: int, m: int, wplus: int) -> int:
+    """Algorithmic bytes of one counting pass: dag_ptr of every u (4(n+1)),
+    each out-list read once to build its table (4m), the bounds of N+(v) for
+    every out-edge (8m) and every probed 2-hop key (4 W+)."""
+    return 4 * (n + 1) + 4 * m + 8 * m + 4 * wplus
+
+
+# -------------------------------------------------------------- the arms
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    import paper_2103_08053_gb300 as T
+
+    rank, local_rank, world = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+
+    t0 = time.time()
+    g = make_graph(WORKLOAD)
+    log(f"[rank {rank}] generated {WORKLOAD['name']}: n={g.n} m={g.m} in {time.time() - t0:.1f}s")
+    bits = 32 if g.nnz < 2 ** 31 else 64
+    rp_h = g.row_ptr.astype(np.int32 if bits == 32 else np.int64)
+    col_h = np.ascontiguousarray(g.col, dtype=np.int32)
+    rp = torch.from_numpy(rp_h).to(dev)
+    col = torch.from_numpy(col_h).to(dev)
+    params = dict(record_timing=1, shard_count=world, shard_index=rank)
+    ctx = T.Context(local_rank, params=params)
+    stream = torch.cuda.current_stream(dev)
+
+    # exact statistics of the DAG (outside the timed region): W+ for the byte model
+    full = T.Context(local_rank)
+    dag = full.orient(g.n, rp, col)
+    st = full.dag_stats(dag)
+    dag.free()
+    full.close()
+
+    out = torch.zeros(1, dtype=torch.int64, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    for _ in range(args.warmup):
+        ctx.count_async(g.n, rp, col, out, err, stream=stream)
+    torch.cuda.synchronize(dev)
+    my_count = int(out.item())
+    if int(err.item()) != 0:
+        raise SystemExit(f"counting failed with status {int(err.item())}")
+    ctx.read_timing()  # drop warm-up timings
+    launches0 = ctx.kernel_launches()
+
+    sampler = ClockSampler(local_rank)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.count_async(g.n, rp, col, out, err, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed_ms = e0.elapsed_time(e1)
+    launches = ctx.kernel_launches() - launches0
+    tm = ctx.read_timing()
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        c = torch.tensor([my_count], dtype=torch.int64, device=dev)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        total_count = int(c.item())
+    else:
+        total_count = my_count
+    ms_per_step = elapsed_ms / args.steps
+    value = g.m / (ms_per_step / 1e3)
+
+    # end to end through the C ABI from pinned host memory: H2D of the CSR, the
+    # whole path, D2H of the count, every step
+    rp_pin = torch.from_numpy(rp_h).pin_memory()
+    col_pin = torch.from_numpy(col_h).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+    ctx.count_host(g.n, rp_pin.numpy(), col_pin.numpy(), stream=stream)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    t_e = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.count_host(g.n, rp_pin.numpy(), col_pin.numpy(), stream=stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = (time.perf_counter() - t_e) * 1e3 / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    ctx.read_timing()
+    ctx.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_src = measured_hbm_peak()
+    count_ms = tm["count_ms"] / max(tm["calls"], 1)
+    bytes_count = count_phase_bytes(g.n, g.m, st["wedges_plus"])
+    achieved = bytes_count / (count_ms / 1e3) / 1e9
+    traffic = profiled_traffic()
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD["name"], "n": g.n, "m": g.m, "nnz": g.nnz, "offset_bits": bits,
+            "triangles": total_count, "wedges_plus": st["wedges_plus"], "max_out_degree": st["max_out_degree"],
+            "bins": {"skip": st["n_skip"], "warp": st["n_warp"], "block": st["n_block"]},
+            "step": "tc_count_async: orientation + binning + hash build/probe + reduction, CSR resident in HBM",
+            "l2": "no flush: inputs larger than L2 (col %.2f GB, DAG %.2f GB vs 129 MB)"
+                  % (g.nnz * 4 / 1e9, (g.m + g.n) * 4 / 1e9),
+            "parallelism": f"workload partition u % {world}" if world > 1 else "single GPU",
+        },
+        "phases_ms": {"orient": tm["orient_ms"] / max(tm["calls"], 1), "bin": tm["bin_ms"] / max(tm["calls"], 1),
+                      "count": count_ms},
+        "roofline": {"kernel": "counting kernels (k_count_block + k_count_pack)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                     else "fallback 6.8 TB/s", "traffic": traffic,
+                     "algorithmic_bytes_per_launch": bytes_count,
+                     "bytes_model": "4(n+1) + 12m + 4W+"},
+        "e2e": {"value": g.m / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(rp_h.nbytes + col_h.nbytes), "d2h_bytes_per_step": 16,
+                "api": "tc_count_host (pinned host CSR)"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        cores = oracle.max_threads()
+        t = time.perf_counter()
+        want = oracle.count(g, threads=cores)
+        cpu_s = time.perf_counter() - t
+        result["cpu_baseline"] = {"value": g.m / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                  "sample": f"one oracle orientation + node-iterator count of the whole "
+                                            f"{WORKLOAD['name']} graph ({cpu_s:.1f} s)"}
+        result["parity"] = {"oracle": want, "gpu": total_count, "equal": want == total_count}
+    if dist:
+        dist.destroy_process_group()
+    print(json.dumps(result), flush=True)
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return  # the CPU oracle runs once, on rank 0
+    import oracle
+    g = make_graph(REF_SAMPLE)
+    cores = oracle.max_threads()
+    for _ in range(args.warmup):
+        oracle.count(g, threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.count(g, threads=cores)
+        times.append(time.perf_counter() - t)
+    ms = 1e3 * sum(times) / len(times)
+    value = g.m / (ms / 1e3)
+    sample = (f"one oracle orientation + node-iterator count per step of {REF_SAMPLE['name']} "
+              f"(same family as {WORKLOAD['name']}, 1/4 of its points), {cores} threads")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "sample": REF_SAMPLE["name"], "n": g.n, "m": g.m},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -106,7 +106,8 @@ typedef struct {
     int32_t shard_count;         /* workload partition (Sec. 5.1): count only u with */
     int32_t shard_index;         /*   u % shard_count == shard_index (default 1 / 0) */
     int32_t validate;            /* reserved for extra input checks (0) */
-    int32_t reserved[4];
+    int32_t record_timing;       /* 1: record CUDA events around the kernel phases (tc_read_timing) */
+    int32_t reserved[3];
 } tc_params;
 
 /* Per-DAG statistics (tc_dag_stats), all exact:
@@ -205,6 +206,23 @@ tc_status tc_poll(tc_ctx* ctx, uint64_t ticket, uint64_t* count);
 tc_status tc_drain(tc_ctx* ctx);
 
 /* ---- diagnostics ---------------------------------------------------------- */
+
+/* Kernel-phase times of the calls made since the last tc_read_timing, from
+ * CUDA events the library records on the caller's stream around its own
+ * launches while tc_params.record_timing is 1 (tc_count, tc_count_async,
+ * tc_count_dag). Sums over the calls, in milliseconds. */
+typedef struct {
+    int64_t calls;
+    double orient_ms;  /* degree, keep counts, scan, compaction */
+    double bin_ms;     /* out-degree binning */
+    double count_ms;   /* hash build + probe + reduction (thread-block and warp workers) */
+} tc_timing;
+
+/* Wait for the recorded events, return the sums and start a new period. */
+tc_status tc_read_timing(tc_ctx* ctx, tc_timing* out);
+
+/* Number of kernels this context has launched so far. */
+tc_status tc_kernel_launches(tc_ctx* ctx, int64_t* out);
 
 const char* tc_status_string(tc_status s);
 /* Text of the last failure on ctx (empty if none); with ctx == NULL, the last

@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _tc
 from ._tc import (TC_ERR_BAD_GRAPH, TC_ERR_BUSY, TC_ERR_CUDA, TC_ERR_INVALID_ARG, TC_ERR_NOT_READY, TC_ERR_OOM,
-                  TC_ERR_TIMEOUT, TC_ERR_UNSUPPORTED, TC_OK, tc_csr, tc_dag, tc_params, tc_stats)
+                  TC_ERR_TIMEOUT, TC_ERR_UNSUPPORTED, TC_OK, tc_csr, tc_dag, tc_params, tc_stats, tc_timing)
 
 __all__ = ["Context", "TcError", "Dag", "default_params", "tc_csr", "tc_dag", "tc_params", "tc_stats"]
 
@@ -191,6 +191,17 @@ class Context:
         s = tc_stats()
         self._check(_tc.tc_dag_stats(self.handle, ctypes.byref(d), ctypes.byref(s), _stream_handle(stream)))
         return {f: int(getattr(s, f)) for f, _ in tc_stats._fields_}
+
+    # diagnostics
+    def read_timing(self) -> dict:
+        t = tc_timing()
+        self._check(_tc.tc_read_timing(self.handle, ctypes.byref(t)))
+        return {f: getattr(t, f) for f, _ in tc_timing._fields_}
+
+    def kernel_launches(self) -> int:
+        v = ctypes.c_int64()
+        self._check(_tc.tc_kernel_launches(self.handle, ctypes.byref(v)))
+        return int(v.value)
 
     # batch
     def count_batch(self, graphs, stream=None) -> list:

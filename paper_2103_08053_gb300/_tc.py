@@ -51,7 +51,12 @@ class tc_params(ctypes.Structure):
                 ("max_levels", c_int32), ("block_threads", c_int32), ("block_smem_bytes", c_int32),
                 ("item_neighbors", c_int32), ("chunk", c_int32), ("warps_per_block", c_int32),
                 ("shard_count", c_int32), ("shard_index", c_int32), ("validate", c_int32),
-                ("reserved", c_int32 * 4)]
+                ("record_timing", c_int32), ("reserved", c_int32 * 3)]
+
+
+class tc_timing(ctypes.Structure):
+    _fields_ = [("calls", c_int64), ("orient_ms", ctypes.c_double), ("bin_ms", ctypes.c_double),
+                ("count_ms", ctypes.c_double)]
 
 
 class tc_stats(ctypes.Structure):
@@ -79,6 +84,8 @@ _protos = {
     "tc_submit": (c_int32, [c_void_p, _P(tc_csr), _P(c_uint64)]),
     "tc_poll": (c_int32, [c_void_p, c_uint64, _P(c_uint64)]),
     "tc_drain": (c_int32, [c_void_p]),
+    "tc_read_timing": (c_int32, [c_void_p, _P(tc_timing)]),
+    "tc_kernel_launches": (c_int32, [c_void_p, _P(c_int64)]),
     "tc_status_string": (ctypes.c_char_p, [c_int32]),
     "tc_last_error": (ctypes.c_char_p, [c_void_p]),
     "tc_version": (ctypes.c_char_p, []),

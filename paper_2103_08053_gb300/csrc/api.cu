@@ -126,6 +126,7 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         TAKE(shard_count);
         p.shard_index = in->shard_index;
         p.validate = in->validate;
+        p.record_timing = in->record_timing;
 #undef TAKE
     }
     if (p.warp_max_out_degree < 1 || p.warp_max_out_degree > 255)
@@ -173,6 +174,7 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         cfg->chunk = p.chunk;
         cfg->shard_count = p.shard_count;
         cfg->shard_index = p.shard_index;
+        cfg->record_timing = p.record_timing ? 1 : 0;
         cfg->warp_grid = cfg->block_grid = 0;
     }
     return TC_OK;
@@ -211,31 +213,61 @@ tc_status tcg::ensure_orient_ws(tc_ctx* ctx, Workspace& ws, int64_t n, int64_t n
     return ensure_count_ws(ctx, ws, n, nnz / 2, st);
 }
 
+// ---- phase timing (tc_params.record_timing) ----------------------------------
+
+TimedCall* tcg::timing_begin(tc_ctx* ctx, bool oriented) {
+    if (!ctx->cfg.record_timing) return nullptr;
+    TimedCall tc;
+    if (!ctx->timed_free.empty()) {
+        tc = ctx->timed_free.back();
+        ctx->timed_free.pop_back();
+    } else {
+        for (int i = 0; i < 4; ++i)
+            if (cudaEventCreate(&tc.ev[i]) != cudaSuccess) {
+                cudaGetLastError();
+                for (int j = 0; j < i; ++j) cudaEventDestroy(tc.ev[j]);
+                return nullptr;
+            }
+    }
+    tc.oriented = oriented;
+    ctx->timed.push_back(tc);
+    return &ctx->timed.back();
+}
+
+void tcg::timing_mark(TimedCall* tc, int i, cudaStream_t st) {
+    if (tc) cudaEventRecord(tc->ev[i], st);
+}
+
 // Enqueue orientation into (dag_ptr, dag_col[cap]) using ws scratch.
 static tc_status enqueue_orient(tc_ctx* ctx, Workspace& ws, const tc_csr* g, int32_t* dag_ptr, int32_t* dag_col,
                                 int64_t cap, cudaStream_t st) {
     DevCounters* ctr = (DevCounters*)ws.ctr.p;
     cudaError_t e = launch_orient(g->row_ptr, g->offset_bits, g->col, g->n, g->nnz, (int32_t*)ws.deg.p,
                                   (int32_t*)ws.kept.p, (long long*)ws.partial.p, dag_ptr, dag_col, cap, ctr,
-                                  ctx->num_sms, st);
+                                  ctx->num_sms, st, &ctx->launches);
     if (g->n == 0 && e == cudaSuccess) e = cudaMemsetAsync(dag_ptr, 0, sizeof(int32_t), st);
     return cuda_status(ctx, e, "orientation kernels");
 }
 
+// Binning + counting; tm (may be null) gets events 2 (after binning) and 3.
 static tc_status enqueue_count(tc_ctx* ctx, Workspace& ws, const int32_t* dag_ptr, const int32_t* dag_col,
-                               int64_t n, uint64_t* per_vertex, cudaStream_t st) {
+                               int64_t n, uint64_t* per_vertex, cudaStream_t st, TimedCall* tm) {
     DevCounters* ctr = (DevCounters*)ws.ctr.p;
     cudaError_t e = cudaSuccess;
     if (per_vertex && n > 0) e = cudaMemsetAsync(per_vertex, 0, (size_t)n * 8, st);
     if (e == cudaSuccess && n > 0) {
         const int64_t m_cap = ws.items.bytes / sizeof(int2);
         e = launch_bin(dag_ptr, n, ctx->cfg, (int32_t*)ws.warp_list.p, (int2*)ws.warp_desc.p, (int2*)ws.items.p,
-                       m_cap, ctr, ctx->num_sms, st);
+                       m_cap, ctr, ctx->num_sms, st, &ctx->launches);
+        timing_mark(tm, 2, st);
         if (e == cudaSuccess)
             e = launch_count(dag_ptr, dag_col, n, (const int32_t*)ws.warp_list.p, (const int2*)ws.warp_desc.p,
-                             (const int2*)ws.items.p,
-                             (unsigned long long*)per_vertex, ctx->cfg, ctr, st);
+                             (const int2*)ws.items.p, (unsigned long long*)per_vertex, ctx->cfg, ctr, st,
+                             &ctx->launches);
+    } else {
+        timing_mark(tm, 2, st);
     }
+    timing_mark(tm, 3, st);
     return cuda_status(ctx, e, "counting kernels");
 }
 
@@ -304,6 +336,11 @@ tc_status tc_destroy(tc_ctx* ctx) {
         ctx->ws.release_all(ctx);
         ctx->out_scalars.release(ctx);
         ctx->csr_copy.release_all(ctx);
+        for (auto* v : {&ctx->timed, &ctx->timed_free})
+            for (auto& t : *v)
+                for (int i = 0; i < 4; ++i) cudaEventDestroy(t.ev[i]);
+        ctx->timed.clear();
+        ctx->timed_free.clear();
         for (auto& kv : ctx->dags) {
             cudaFree(kv.first);
             cudaFree(kv.second);
@@ -403,7 +440,10 @@ tc_status tc_count_dag(tc_ctx* ctx, const tc_dag* dag, uint64_t* count_host, uin
     tc_status s = ensure_count_ws(ctx, ctx->ws, dag->n, dag->m, st);
     if (s) return s;
     s = cuda_status(ctx, cudaMemsetAsync(ctx->ws.ctr.p, 0, sizeof(DevCounters), st), "memset counters");
-    if (!s) s = enqueue_count(ctx, ctx->ws, dag->dag_ptr, dag->dag_col, dag->n, per_vertex_device, st);
+    TimedCall* tm = timing_begin(ctx, false);
+    timing_mark(tm, 0, st);
+    timing_mark(tm, 1, st);
+    if (!s) s = enqueue_count(ctx, ctx->ws, dag->dag_ptr, dag->dag_col, dag->n, per_vertex_device, st, tm);
     DevCounters c;
     if (!s) s = read_counters(ctx, ctx->ws, st, &c);
     if (s) return s;
@@ -423,11 +463,15 @@ tc_status tc_count_async(tc_ctx* ctx, const tc_csr* g, uint64_t* count_device, i
     if ((s = ws.dag_ptr.ensure(ctx, (size_t)(g->n + 1) * 4, st))) return s;
     if ((s = ws.dag_col.ensure(ctx, (size_t)(g->nnz / 2 + 1) * 4, st))) return s;
     s = cuda_status(ctx, cudaMemsetAsync(ws.ctr.p, 0, sizeof(DevCounters), st), "memset counters");
+    TimedCall* tm = s ? nullptr : timing_begin(ctx, true);
+    timing_mark(tm, 0, st);
     if (!s) s = enqueue_orient(ctx, ws, g, (int32_t*)ws.dag_ptr.p, (int32_t*)ws.dag_col.p, g->nnz / 2 + 1, st);
-    if (!s) s = enqueue_count(ctx, ws, (int32_t*)ws.dag_ptr.p, (int32_t*)ws.dag_col.p, g->n, nullptr, st);
+    timing_mark(tm, 1, st);
+    if (!s) s = enqueue_count(ctx, ws, (int32_t*)ws.dag_ptr.p, (int32_t*)ws.dag_col.p, g->n, nullptr, st, tm);
     if (!s)
         s = cuda_status(ctx,
-                        launch_finish((DevCounters*)ws.ctr.p, (unsigned long long*)count_device, error_device, st),
+                        launch_finish((DevCounters*)ws.ctr.p, (unsigned long long*)count_device, error_device, st,
+                                      &ctx->launches),
                         "finish kernel");
     return s;
 }
@@ -495,6 +539,36 @@ tc_status tc_dag_stats(tc_ctx* ctx, const tc_dag* dag, tc_stats* out, void* stre
     out->n_block = h.n_block;
     out->wedges_plus = (int64_t)h.wplus;
     out->wedges_plus_block = (int64_t)h.wplus_block;
+    return TC_OK;
+}
+
+tc_status tc_read_timing(tc_ctx* ctx, tc_timing* out) {
+    if (!ctx || !out) return TC_ERR_INVALID_ARG;
+    DeviceGuard dg(ctx->device);
+    tc_timing t{};
+    tc_status s = TC_OK;
+    for (auto& c : ctx->timed) {
+        float a = 0.f, b = 0.f, d = 0.f;
+        cudaError_t e = cudaEventSynchronize(c.ev[3]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&a, c.ev[0], c.ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&b, c.ev[1], c.ev[2]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&d, c.ev[2], c.ev[3]);
+        if (e != cudaSuccess && !s) s = cuda_status(ctx, e, "reading timing events");
+        t.calls++;
+        t.orient_ms += a;
+        t.bin_ms += b;
+        t.count_ms += d;
+        ctx->timed_free.push_back(c);
+    }
+    ctx->timed.clear();
+    if (s) return s;
+    *out = t;
+    return TC_OK;
+}
+
+tc_status tc_kernel_launches(tc_ctx* ctx, int64_t* out) {
+    if (!ctx || !out) return TC_ERR_INVALID_ARG;
+    *out = ctx->launches;
     return TC_OK;
 }
 

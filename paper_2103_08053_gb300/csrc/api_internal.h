@@ -50,6 +50,13 @@ class DeviceGuard {
     int prev_ = -1, dev_ = -1;
 };
 
+// CUDA events of one timed call: [0] before orientation (or binning), [1]
+// after orientation, [2] after binning, [3] after the counting kernels.
+struct TimedCall {
+    cudaEvent_t ev[4];
+    bool oriented;
+};
+
 struct BatchState;  // batch.cu
 struct ServeState;  // serve.cu
 
@@ -69,6 +76,9 @@ struct tc_ctx {
     tcg::BufPair csr_copy;            // device copy of a host CSR (tc_count_host)
     tcg::DevCounters* host_ctr = nullptr;  // pinned
     std::map<void*, void*> dags;      // tc_orient allocations: dag_ptr -> dag_col
+    long long launches = 0;                 // kernels launched by this context
+    std::vector<tcg::TimedCall> timed;      // recorded, not yet read
+    std::vector<tcg::TimedCall> timed_free; // event sets to reuse
     tcg::BatchState* batch = nullptr;
     tcg::ServeState* serve = nullptr;
 };
@@ -85,6 +95,10 @@ tc_status ensure_count_ws(tc_ctx* ctx, Workspace& ws, int64_t n, int64_t m, cuda
 tc_status ensure_orient_ws(tc_ctx* ctx, Workspace& ws, int64_t n, int64_t nnz, cudaStream_t st);
 
 void batch_release(tc_ctx* ctx);  // batch.cu
+// Start a timed call when tc_params.record_timing is set (else returns null);
+// mark(i) records event i of it on st.
+TimedCall* timing_begin(tc_ctx* ctx, bool oriented);
+void timing_mark(TimedCall* tc, int i, cudaStream_t st);
 void serve_shutdown(tc_ctx* ctx); // serve.cu
 
 }  // namespace tcg

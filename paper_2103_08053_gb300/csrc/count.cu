@@ -574,7 +574,8 @@ cudaError_t count_kernel_setup(CountCfg& cfg, int num_sms) {
 
 cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t n, const int32_t* warp_list,
                          const int2* warp_desc, const int2* items, unsigned long long* per_vertex,
-                         const CountCfg& cfg, DevCounters* ctr, cudaStream_t st) {
+                         const CountCfg& cfg, DevCounters* ctr, cudaStream_t st, long long* launches) {
+    *launches += 2;
     const int budget = count_block_budget_ints(cfg);
     int part_max = 1;
     while (part_max * 2 * 3 <= budget) part_max *= 2;
@@ -586,7 +587,9 @@ cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_finish(const DevCounters* ctr, unsigned long long* count_out, int* err_out, cudaStream_t st) {
+cudaError_t launch_finish(const DevCounters* ctr, unsigned long long* count_out, int* err_out, cudaStream_t st,
+                          long long* launches) {
+    *launches += 1;
     k_finish<<<1, 1, 0, st>>>(ctr, count_out, err_out);
     return cudaGetLastError();
 }

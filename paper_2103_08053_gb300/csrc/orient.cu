@@ -286,8 +286,9 @@ __global__ void k_bin(const int32_t* __restrict__ dag_ptr, int64_t n, int warp_m
 template <typename Off>
 cudaError_t orient_t(const Off* row_ptr, const int32_t* col, int64_t n, int64_t nnz, int32_t* deg, int32_t* kept,
                      long long* partial, int32_t* dag_ptr, int32_t* dag_col, int64_t dag_cap, DevCounters* ctr,
-                     int num_sms, cudaStream_t st) {
+                     int num_sms, cudaStream_t st, long long* launches) {
     if (n <= 0) return cudaSuccess;
+    *launches += 6;
     const int64_t groups = (n + 31) / 32;
     int og = (int)((groups + ORIENT_WARPS - 1) / ORIENT_WARPS);
     const int og_cap = num_sms * 8 * 4;
@@ -311,17 +312,19 @@ int scan_blocks(int64_t n) { return (int)((n + SCAN_TILE - 1) / SCAN_TILE); }
 
 cudaError_t launch_orient(const void* row_ptr, int offset_bits, const int32_t* col, int64_t n, int64_t nnz,
                           int32_t* deg, int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
-                          int64_t dag_cap, DevCounters* ctr, int num_sms, cudaStream_t st) {
+                          int64_t dag_cap, DevCounters* ctr, int num_sms, cudaStream_t st, long long* launches) {
     if (offset_bits == 64)
         return orient_t(static_cast<const long long*>(row_ptr), col, n, nnz, deg, kept, partial, dag_ptr, dag_col,
-                        dag_cap, ctr, num_sms, st);
+                        dag_cap, ctr, num_sms, st, launches);
     return orient_t(static_cast<const int32_t*>(row_ptr), col, n, nnz, deg, kept, partial, dag_ptr, dag_col, dag_cap,
-                    ctr, num_sms, st);
+                    ctr, num_sms, st, launches);
 }
 
 cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* warp_desc,
-                       int2* items, int64_t item_cap, DevCounters* ctr, int num_sms, cudaStream_t st) {
+                       int2* items, int64_t item_cap, DevCounters* ctr, int num_sms, cudaStream_t st,
+                       long long* launches) {
     if (n <= 0) return cudaSuccess;
+    *launches += 1;
     int g = (int)((n + 255) / 256);
     if (g > num_sms * 16) g = num_sms * 16;
     k_bin<<<g, 256, 0, st>>>(dag_ptr, n, cfg.warp_max_out_degree, cfg.item_neighbors, cfg.shard_count,

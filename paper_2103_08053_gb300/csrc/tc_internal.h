@@ -46,6 +46,7 @@ struct CountCfg {
     int item_neighbors;
     int chunk;
     int shard_count, shard_index;
+    int record_timing;
 };
 
 // ---- orientation (orient.cu) ----------------------------------------------
@@ -54,21 +55,23 @@ struct CountCfg {
 int scan_blocks(int64_t n);
 cudaError_t launch_orient(const void* row_ptr, int offset_bits, const int32_t* col, int64_t n, int64_t nnz,
                           int32_t* deg, int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
-                          int64_t dag_cap, DevCounters* ctr, int num_sms, cudaStream_t st);
+                          int64_t dag_cap, DevCounters* ctr, int num_sms, cudaStream_t st, long long* launches);
 
 // Binning (Sec. 4.3) from an existing DAG: fills warp_list / items / counters.
 cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* warp_desc,
-                       int2* items, int64_t item_cap, DevCounters* ctr, int num_sms, cudaStream_t st);
+                       int2* items, int64_t item_cap, DevCounters* ctr, int num_sms, cudaStream_t st,
+                       long long* launches);
 
 // ---- counting (count.cu) ----------------------------------------------------
 cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t n, const int32_t* warp_list,
                          const int2* warp_desc, const int2* items, unsigned long long* per_vertex,
-                         const CountCfg& cfg, DevCounters* ctr, cudaStream_t st);
+                         const CountCfg& cfg, DevCounters* ctr, cudaStream_t st, long long* launches);
 int count_block_budget_ints(const CountCfg& cfg);
 // ints of one warp-worker table for out-degree d (2*nextpow2(d) buckets of 4 slots + byte lengths)
 int pack_table_ints(int max_out_degree, int min_buckets);
 cudaError_t count_kernel_setup(CountCfg& cfg, int num_sms);
-cudaError_t launch_finish(const DevCounters* ctr, unsigned long long* count_out, int* err_out, cudaStream_t st);
+cudaError_t launch_finish(const DevCounters* ctr, unsigned long long* count_out, int* err_out, cudaStream_t st,
+                          long long* launches);
 
 // stats: W+ (total and block part), max d+
 struct DevStats {

@@ -281,3 +281,15 @@ def test_invalid_params(T):
         with pytest.raises(T.TcError) as ei:
             T.Context(0, params=bad)
         assert ei.value.status == T.TC_ERR_INVALID_ARG
+
+
+def test_phase_timing_and_launch_count(T):
+    g = G.rmat(13, 16, seed=20)
+    with T.Context(0, params=dict(record_timing=1)) as c:
+        rp, col = dev(g)
+        l0 = c.kernel_launches()
+        assert c.count(g.n, rp, col) == oracle.count(g)
+        assert c.kernel_launches() - l0 == 10   # 6 orientation + bin + 2 counting + finish
+        t = c.read_timing()
+        assert t["calls"] == 1 and t["orient_ms"] > 0 and t["count_ms"] > 0
+        assert c.read_timing()["calls"] == 0
