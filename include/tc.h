@@ -179,6 +179,36 @@ tc_status tc_count_host(tc_ctx* ctx, const tc_csr* g, uint64_t* count_host, void
 /* Exact statistics of an oriented graph (out-degree bins, W+). Blocks. */
 tc_status tc_dag_stats(tc_ctx* ctx, const tc_dag* dag, tc_stats* out, void* stream);
 
+/* ---- counting without device allocation ------------------------------------- */
+
+/* The paper has no counterpart to this entry point. It is for callers that
+ * cannot allocate device memory: code whose GPU memory is entirely reserved by
+ * another allocator (for example a framework's caching pool), and
+ * latency-critical loops that must not call cudaMalloc/cudaFree, which can
+ * synchronise the whole device. It needs no context and allocates nothing.
+ *
+ * It counts the triangles of an oriented graph exactly like tc_count_dag with
+ * the default tc_params (no per-vertex output), using a scratch array that is a
+ * static part of the library on every device that loads it (about 5.3 MB, held
+ * until the process exits). dag: device arrays, caller-owned, with
+ * n <= TC_NOALLOC_MAX_N and m <= TC_NOALLOC_MAX_M; larger graphs are rejected
+ * with TC_ERR_UNSUPPORTED before any GPU work. count_device: device uint64,
+ * receives the count; error_device: device int32 (may be NULL), receives a
+ * tc_status for malformed input (out-of-range neighbour ids). Asynchronous on
+ * `stream`; the outputs are valid once the stream reaches this work.
+ *
+ * The first call on each device sets that device up (it looks up the scratch
+ * array's device address and configures the kernels, with that device
+ * current); make that first call before any stream capture. All calls on a
+ * device share the one scratch array: calls whose work overlaps on the GPU
+ * (different streams, or different host threads) race and give wrong counts;
+ * serialise them on one stream. The scratch keeps the previous call's contents;
+ * each call clears what must start at zero. Failures that happen before any GPU
+ * work are described by tc_last_error(NULL). */
+#define TC_NOALLOC_MAX_N 262144
+#define TC_NOALLOC_MAX_M 16777216
+tc_status tc_count_dag_noalloc(const tc_dag* dag, uint64_t* count_device, int32_t* error_device, void* stream);
+
 /* ---- batched counting ----------------------------------------------------- */
 
 /* Count k independent graphs in one pass: all graphs are oriented by one

@@ -85,6 +85,7 @@ _protos = {
     "tc_poll": (c_int32, [c_void_p, c_uint64, _P(c_uint64)]),
     "tc_drain": (c_int32, [c_void_p]),
     "tc_read_timing": (c_int32, [c_void_p, _P(tc_timing)]),
+    "tc_count_dag_noalloc": (c_int32, [_P(tc_dag), c_void_p, c_void_p, c_void_p]),
     "tc_kernel_launches": (c_int32, [c_void_p, _P(c_int64)]),
     "tc_status_string": (ctypes.c_char_p, [c_int32]),
     "tc_last_error": (ctypes.c_char_p, [c_void_p]),

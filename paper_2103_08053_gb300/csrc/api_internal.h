@@ -95,6 +95,7 @@ tc_status ensure_count_ws(tc_ctx* ctx, Workspace& ws, int64_t n, int64_t m, cuda
 tc_status ensure_orient_ws(tc_ctx* ctx, Workspace& ws, int64_t n, int64_t nnz, cudaStream_t st);
 
 void batch_release(tc_ctx* ctx);  // batch.cu
+size_t noalloc_scratch_bytes();    // noalloc.cu
 // Start a timed call when tc_params.record_timing is set (else returns null);
 // mark(i) records event i of it on st.
 TimedCall* timing_begin(tc_ctx* ctx, bool oriented);
