@@ -364,6 +364,7 @@ tc_status tc_set_params(tc_ctx* ctx, const tc_params* p) {
     if (s) return s;
     ctx->params = np;
     ctx->cfg = cfg;
+    ctx->cfg_version++;
     return TC_OK;
 }
 

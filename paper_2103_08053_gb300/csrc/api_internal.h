@@ -57,7 +57,35 @@ struct TimedCall {
     bool oriented;
 };
 
-struct BatchState;  // batch.cu
+// One batched counting pass (batch.cu): its own stream, workspace, pinned
+// staging and a CUDA graph of the whole launch sequence, replayed while the
+// batch shape (graph count, padded vertices, entries, offset width, params)
+// and the buffers stay the same. Used by tc_count_batch and by serving rounds.
+struct BatchRunner {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_done = nullptr;
+    Workspace ws;
+    DevBuf graphs, per_vertex, counts, dag_ptr, dag_col;
+    GraphRef* h_graphs = nullptr;   // pinned
+    uint64_t* h_counts = nullptr;   // pinned
+    DevCounters* h_ctr = nullptr;   // pinned
+    int h_cap = 0;
+    int k = 0, bits = 32;
+    long long total = 0, nnz_total = 0;
+    bool moved = true;              // a buffer moved since the graph was captured
+    cudaGraphExec_t exec = nullptr;
+    int key_k = -1, key_bits = 0;
+    long long key_total = 0, key_nnz = 0, key_cfg = -1, captured_launches = 0;
+
+    tc_status init(tc_ctx* ctx);
+    void release(tc_ctx* ctx);
+    void drop_graph();
+    tc_status prepare(tc_ctx* ctx, const tc_csr* gs, int k);  // layout + buffers + staging
+    tc_status enqueue(tc_ctx* ctx);                           // the launch sequence on `stream`
+    tc_status launch(tc_ctx* ctx, bool use_graph);            // capture once, then replay
+    tc_status finish(tc_ctx* ctx, uint64_t* counts_host);     // wait, check errors, copy results
+};
+
 struct ServeState;  // serve.cu
 
 }  // namespace tcg
@@ -79,7 +107,8 @@ struct tc_ctx {
     long long launches = 0;                 // kernels launched by this context
     std::vector<tcg::TimedCall> timed;      // recorded, not yet read
     std::vector<tcg::TimedCall> timed_free; // event sets to reuse
-    tcg::BatchState* batch = nullptr;
+    long long cfg_version = 0;              // bumped by tc_set_params
+    tcg::BatchRunner* batch = nullptr;
     tcg::ServeState* serve = nullptr;
 };
 

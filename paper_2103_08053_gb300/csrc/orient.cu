@@ -28,16 +28,37 @@ namespace {
 __device__ __forceinline__ unsigned lanemask_le(int lane) { return (2u << lane) - 1u; }
 __device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
 
-template <typename Off>
-__global__ void k_degree(const Off* __restrict__ row_ptr, int64_t n, int64_t nnz, int32_t* __restrict__ deg,
-                         DevCounters* ctr) {
+// The graph owning global row `row`: the single graph, or for a batch the
+// last graph whose vertex base is <= row (bases ascending, multiples of 32).
+template <bool BATCH>
+__device__ __forceinline__ GraphRef graph_of(int64_t row, const GraphRef& one, const GraphRef* __restrict__ gs,
+                                             int k) {
+    if (!BATCH) return one;
+    int lo = 0, hi = k;  // first graph with vbase > row
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (gs[mid].vbase <= row) lo = mid + 1;
+        else hi = mid;
+    }
+    return gs[lo - 1];
+}
+
+template <typename Off, bool BATCH>
+__global__ void k_degree(GraphRef one, const GraphRef* __restrict__ gs, int k, int64_t total,
+                         int32_t* __restrict__ deg, DevCounters* ctr) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
-        const long long a = (long long)row_ptr[u], b = (long long)row_ptr[u + 1];
-        long long d = b - a;
-        if (a < 0 || d < 0 || b > nnz || d > 0x7fffffffLL) {
-            atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
-            d = 0;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < total; u += stride) {
+        const GraphRef G = graph_of<BATCH>(u, one, gs, k);
+        const int64_t ul = u - G.vbase;
+        long long d = 0;
+        if (ul < G.n) {
+            const Off* rp = static_cast<const Off*>(G.row_ptr);
+            const long long a = (long long)rp[ul], b = (long long)rp[ul + 1];
+            d = b - a;
+            if (a < 0 || d < 0 || b > G.nnz || d > 0x7fffffffLL) {
+                atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
+                d = 0;
+            }
         }
         deg[u] = (int32_t)d;
     }
@@ -48,11 +69,14 @@ constexpr int ORIENT_WARPS = ORIENT_THREADS / 32;
 constexpr int ORIENT_UNROLL = 4;
 
 // COMPACT == false: kept[u] = out-degree. COMPACT == true: write dag_col.
-template <typename Off, bool COMPACT>
+// Global row space [0, total); a batch pads every graph to a multiple of 32
+// rows, so a 32-row warp group never spans two graphs. deg, kept, dag_ptr
+// and the DAG's neighbour ids are global (vbase + local id).
+template <typename Off, bool COMPACT, bool BATCH>
 __global__ void __launch_bounds__(ORIENT_THREADS)
-    k_orient(const Off* __restrict__ row_ptr, const int32_t* __restrict__ col, const int32_t* __restrict__ deg,
-             int64_t n, int64_t nnz, int32_t* __restrict__ kept, const int32_t* __restrict__ dag_ptr,
-             int32_t* __restrict__ dag_col, int64_t dag_cap, DevCounters* ctr) {
+    k_orient(GraphRef one, const GraphRef* __restrict__ gs, int k, int64_t total, const int32_t* __restrict__ deg,
+             int32_t* __restrict__ kept, const int32_t* __restrict__ dag_ptr, int32_t* __restrict__ dag_col,
+             int64_t dag_cap, DevCounters* ctr) {
     __shared__ long long s_st[ORIENT_WARPS][33];
     __shared__ int s_cnt[ORIENT_WARPS][32];
     __shared__ int s_dp[ORIENT_WARPS][32];
@@ -63,9 +87,17 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
     long long* st = s_st[w];
     int* cnt = s_cnt[w];
     int* dp = s_dp[w];
-    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g * 32 < n; g += nw) {
-        const int64_t u0 = g * 32;
-        const int nr = (int)(n - u0 < 32 ? n - u0 : 32);
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g * 32 < total; g += nw) {
+        const GraphRef G = graph_of<BATCH>(g * 32, one, gs, k);
+        const Off* row_ptr = static_cast<const Off*>(G.row_ptr);
+        const int32_t* col = G.col;
+        const int64_t n = G.n, nnz = G.nnz, vb = G.vbase;
+        const int64_t u0 = g * 32 - vb;  // local id of the group's first row
+        const int nr = (int)(n - u0 < 32 ? (n - u0 > 0 ? n - u0 : 0) : 32);
+        if (nr == 0) {  // padding rows of a batch
+            if (!COMPACT) kept[g * 32 + lane] = 0;
+            continue;
+        }
         long long e = 0;
         if (lane == 0) e = (long long)row_ptr[u0 + nr];
         e = __shfl_sync(FULL, e, 0);
@@ -80,7 +112,7 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
         st[lane] = a;
         if (lane == 0) st[32] = e;
         cnt[lane] = 0;
-        if (COMPACT) dp[lane] = (lane < nr) ? dag_ptr[u0 + lane] : 0;
+        if (COMPACT) dp[lane] = (lane < nr) ? dag_ptr[g * 32 + lane] : 0;
         __syncwarp();
         const long long gb = __shfl_sync(FULL, a, 0), ge = e;
         int r = 0;
@@ -95,7 +127,7 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
             }
 #pragma unroll
             for (int q = 0; q < ORIENT_UNROLL; ++q)
-                dq[q] = ((unsigned)vq[q] < (unsigned long long)n) ? __ldg(deg + vq[q]) : 0;
+                dq[q] = ((unsigned)vq[q] < (unsigned long long)n) ? __ldg(deg + vb + vq[q]) : 0;
 #pragma unroll
             for (int q = 0; q < ORIENT_UNROLL; ++q) {
                 const long long f = base + 32 * q + lane;
@@ -128,7 +160,7 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
                 if (COMPACT && keep) {
                     const long long pos = (long long)dp[r] + cnt[r] + __popc(km & lt & segbits);
                     if (pos < dag_cap)
-                        dag_col[pos] = v;
+                        dag_col[pos] = (int32_t)(vb + v);
                     else
                         atomicOr(&ctr->err, ERRBIT_DAG_OVERFLOW);
                 }
@@ -137,7 +169,12 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
                 __syncwarp();
             }
         }
-        if (!COMPACT && lane < nr) kept[u0 + lane] = cnt[lane];
+        if (!COMPACT) {
+            if (BATCH)
+                kept[g * 32 + lane] = cnt[lane];  // rows past nr of the graph are padding: 0
+            else if (lane < nr)
+                kept[u0 + lane] = cnt[lane];
+        }
         __syncwarp();
     }
 }
@@ -283,26 +320,27 @@ __global__ void k_bin(const int32_t* __restrict__ dag_ptr, int64_t n, int warp_m
     }
 }
 
-template <typename Off>
-cudaError_t orient_t(const Off* row_ptr, const int32_t* col, int64_t n, int64_t nnz, int32_t* deg, int32_t* kept,
+template <typename Off, bool BATCH>
+cudaError_t orient_t(const GraphRef& one, const GraphRef* gs, int k, int64_t total, int32_t* deg, int32_t* kept,
                      long long* partial, int32_t* dag_ptr, int32_t* dag_col, int64_t dag_cap, DevCounters* ctr,
                      int num_sms, cudaStream_t st, long long* launches) {
-    if (n <= 0) return cudaSuccess;
+    if (total <= 0) return cudaSuccess;
     *launches += 6;
-    const int64_t groups = (n + 31) / 32;
+    const int64_t groups = (total + 31) / 32;
     int og = (int)((groups + ORIENT_WARPS - 1) / ORIENT_WARPS);
     const int og_cap = num_sms * 8 * 4;
     if (og > og_cap) og = og_cap;
-    int dg = (int)((n + 255) / 256);
+    int dg = (int)((total + 255) / 256);
     if (dg > num_sms * 16) dg = num_sms * 16;
-    k_degree<Off><<<dg, 256, 0, st>>>(row_ptr, n, nnz, deg, ctr);
-    k_orient<Off, false><<<og, ORIENT_THREADS, 0, st>>>(row_ptr, col, deg, n, nnz, kept, nullptr, nullptr, 0, ctr);
-    const int nb = scan_blocks(n);
-    k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(kept, n, partial);
-    k_scan_top<<<1, SCAN_TOP_THREADS, 0, st>>>(partial, nb, dag_ptr, n, ctr);
-    k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(kept, n, partial, dag_ptr);
-    k_orient<Off, true><<<og, ORIENT_THREADS, 0, st>>>(row_ptr, col, deg, n, nnz, nullptr, dag_ptr, dag_col, dag_cap,
-                                                       ctr);
+    k_degree<Off, BATCH><<<dg, 256, 0, st>>>(one, gs, k, total, deg, ctr);
+    k_orient<Off, false, BATCH><<<og, ORIENT_THREADS, 0, st>>>(one, gs, k, total, deg, kept, nullptr, nullptr, 0,
+                                                                ctr);
+    const int nb = scan_blocks(total);
+    k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(kept, total, partial);
+    k_scan_top<<<1, SCAN_TOP_THREADS, 0, st>>>(partial, nb, dag_ptr, total, ctr);
+    k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(kept, total, partial, dag_ptr);
+    k_orient<Off, true, BATCH><<<og, ORIENT_THREADS, 0, st>>>(one, gs, k, total, deg, nullptr, dag_ptr, dag_col,
+                                                               dag_cap, ctr);
     return cudaGetLastError();
 }
 
@@ -313,11 +351,24 @@ int scan_blocks(int64_t n) { return (int)((n + SCAN_TILE - 1) / SCAN_TILE); }
 cudaError_t launch_orient(const void* row_ptr, int offset_bits, const int32_t* col, int64_t n, int64_t nnz,
                           int32_t* deg, int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
                           int64_t dag_cap, DevCounters* ctr, int num_sms, cudaStream_t st, long long* launches) {
+    const GraphRef one{row_ptr, col, n, nnz, 0};
     if (offset_bits == 64)
-        return orient_t(static_cast<const long long*>(row_ptr), col, n, nnz, deg, kept, partial, dag_ptr, dag_col,
-                        dag_cap, ctr, num_sms, st, launches);
-    return orient_t(static_cast<const int32_t*>(row_ptr), col, n, nnz, deg, kept, partial, dag_ptr, dag_col, dag_cap,
-                    ctr, num_sms, st, launches);
+        return orient_t<long long, false>(one, nullptr, 1, n, deg, kept, partial, dag_ptr, dag_col, dag_cap, ctr,
+                                          num_sms, st, launches);
+    return orient_t<int32_t, false>(one, nullptr, 1, n, deg, kept, partial, dag_ptr, dag_col, dag_cap, ctr, num_sms,
+                                    st, launches);
+}
+
+cudaError_t launch_orient_batch(const GraphRef* graphs, int k, int offset_bits, int64_t total, int32_t* deg,
+                                int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
+                                int64_t dag_cap, DevCounters* ctr, int num_sms, cudaStream_t st,
+                                long long* launches) {
+    const GraphRef none{nullptr, nullptr, 0, 0, 0};
+    if (offset_bits == 64)
+        return orient_t<long long, true>(none, graphs, k, total, deg, kept, partial, dag_ptr, dag_col, dag_cap, ctr,
+                                         num_sms, st, launches);
+    return orient_t<int32_t, true>(none, graphs, k, total, deg, kept, partial, dag_ptr, dag_col, dag_cap, ctr,
+                                   num_sms, st, launches);
 }
 
 cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* warp_desc,

@@ -49,6 +49,15 @@ struct CountCfg {
     int record_timing;
 };
 
+// One graph of an orientation pass. A batch places its graphs in one padded
+// global vertex space: graph i owns global rows [vbase, vbase + n), vbase a
+// multiple of 32 and ascending; rows in the padding have no edges.
+struct GraphRef {
+    const void* row_ptr;  // int32 or int64 offsets (one width per pass)
+    const int32_t* col;
+    long long n, nnz, vbase;
+};
+
 // ---- orientation (orient.cu) ----------------------------------------------
 // deg, kept: int32[n]; partial: int64[scan_blocks(n)+1]; dag_ptr: int32[n+1];
 // warp_list: int32[n]; warp_desc: int2[n]; items: int2[item_cap].
@@ -56,6 +65,13 @@ int scan_blocks(int64_t n);
 cudaError_t launch_orient(const void* row_ptr, int offset_bits, const int32_t* col, int64_t n, int64_t nnz,
                           int32_t* deg, int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
                           int64_t dag_cap, DevCounters* ctr, int num_sms, cudaStream_t st, long long* launches);
+
+// Orientation of k graphs at once (device array of GraphRef, bases ascending)
+// into one DAG over the padded global vertex space [0, total).
+cudaError_t launch_orient_batch(const GraphRef* graphs, int k, int offset_bits, int64_t total, int32_t* deg,
+                                int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
+                                int64_t dag_cap, DevCounters* ctr, int num_sms, cudaStream_t st,
+                                long long* launches);
 
 // Binning (Sec. 4.3) from an existing DAG: fills warp_list / items / counters.
 cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* warp_desc,
