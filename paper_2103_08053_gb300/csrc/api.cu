@@ -242,9 +242,11 @@ void tcg::timing_mark(TimedCall* tc, int i, cudaStream_t st) {
 static tc_status enqueue_orient(tc_ctx* ctx, Workspace& ws, const tc_csr* g, int32_t* dag_ptr, int32_t* dag_col,
                                 int64_t cap, cudaStream_t st) {
     DevCounters* ctr = (DevCounters*)ws.ctr.p;
+    long long nl = 0;
     cudaError_t e = launch_orient(g->row_ptr, g->offset_bits, g->col, g->n, g->nnz, (int32_t*)ws.deg.p,
                                   (int32_t*)ws.kept.p, (long long*)ws.partial.p, dag_ptr, dag_col, cap, ctr,
-                                  ctx->num_sms, st, &ctx->launches);
+                                  ctx->num_sms, st, &nl);
+    ctx->launches += nl;
     if (g->n == 0 && e == cudaSuccess) e = cudaMemsetAsync(dag_ptr, 0, sizeof(int32_t), st);
     return cuda_status(ctx, e, "orientation kernels");
 }
@@ -254,20 +256,21 @@ static tc_status enqueue_count(tc_ctx* ctx, Workspace& ws, const int32_t* dag_pt
                                int64_t n, uint64_t* per_vertex, cudaStream_t st, TimedCall* tm) {
     DevCounters* ctr = (DevCounters*)ws.ctr.p;
     cudaError_t e = cudaSuccess;
+    long long nl = 0;
     if (per_vertex && n > 0) e = cudaMemsetAsync(per_vertex, 0, (size_t)n * 8, st);
     if (e == cudaSuccess && n > 0) {
         const int64_t m_cap = ws.items.bytes / sizeof(int2);
         e = launch_bin(dag_ptr, n, ctx->cfg, (int32_t*)ws.warp_list.p, (int2*)ws.warp_desc.p, (int2*)ws.items.p,
-                       m_cap, ctr, ctx->num_sms, st, &ctx->launches);
+                       m_cap, ctr, ctx->num_sms, st, &nl);
         timing_mark(tm, 2, st);
         if (e == cudaSuccess)
             e = launch_count(dag_ptr, dag_col, n, (const int32_t*)ws.warp_list.p, (const int2*)ws.warp_desc.p,
-                             (const int2*)ws.items.p, (unsigned long long*)per_vertex, ctx->cfg, ctr, st,
-                             &ctx->launches);
+                             (const int2*)ws.items.p, (unsigned long long*)per_vertex, ctx->cfg, ctr, st, &nl);
     } else {
         timing_mark(tm, 2, st);
     }
     timing_mark(tm, 3, st);
+    ctx->launches += nl;
     return cuda_status(ctx, e, "counting kernels");
 }
 
@@ -469,11 +472,14 @@ tc_status tc_count_async(tc_ctx* ctx, const tc_csr* g, uint64_t* count_device, i
     if (!s) s = enqueue_orient(ctx, ws, g, (int32_t*)ws.dag_ptr.p, (int32_t*)ws.dag_col.p, g->nnz / 2 + 1, st);
     timing_mark(tm, 1, st);
     if (!s) s = enqueue_count(ctx, ws, (int32_t*)ws.dag_ptr.p, (int32_t*)ws.dag_col.p, g->n, nullptr, st, tm);
-    if (!s)
+    if (!s) {
+        long long nl = 0;
         s = cuda_status(ctx,
                         launch_finish((DevCounters*)ws.ctr.p, (unsigned long long*)count_device, error_device, st,
-                                      &ctx->launches),
+                                      &nl),
                         "finish kernel");
+        ctx->launches += nl;
+    }
     return s;
 }
 
@@ -569,7 +575,7 @@ tc_status tc_read_timing(tc_ctx* ctx, tc_timing* out) {
 
 tc_status tc_kernel_launches(tc_ctx* ctx, int64_t* out) {
     if (!ctx || !out) return TC_ERR_INVALID_ARG;
-    *out = ctx->launches;
+    *out = ctx->launches.load();
     return TC_OK;
 }
 

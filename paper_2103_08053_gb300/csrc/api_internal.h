@@ -75,7 +75,7 @@ struct BatchRunner {
     bool moved = true;              // a buffer moved since the graph was captured
     cudaGraphExec_t exec = nullptr;
     int key_k = -1, key_bits = 0;
-    long long key_total = 0, key_nnz = 0, key_cfg = -1, captured_launches = 0;
+    long long key_total = 0, key_nnz = 0, key_cfg = -1, captured_launches = 0, enqueued_launches = 0;
 
     tc_status init(tc_ctx* ctx);
     void release(tc_ctx* ctx);
@@ -104,7 +104,7 @@ struct tc_ctx {
     tcg::BufPair csr_copy;            // device copy of a host CSR (tc_count_host)
     tcg::DevCounters* host_ctr = nullptr;  // pinned
     std::map<void*, void*> dags;      // tc_orient allocations: dag_ptr -> dag_col
-    long long launches = 0;                 // kernels launched by this context
+    std::atomic<long long> launches{0};     // kernels launched by this context (any thread)
     std::vector<tcg::TimedCall> timed;      // recorded, not yet read
     std::vector<tcg::TimedCall> timed_free; // event sets to reuse
     long long cfg_version = 0;              // bumped by tc_set_params

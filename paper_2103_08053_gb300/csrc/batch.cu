@@ -144,35 +144,41 @@ tc_status BatchRunner::prepare(tc_ctx* ctx, const tc_csr* gs, int k) {
 // The whole batch, enqueued on `stream` (also used for capture).
 tc_status BatchRunner::enqueue(tc_ctx* ctx) {
     DevCounters* ctr = (DevCounters*)ws.ctr.p;
+    long long nl = 0;
     cudaError_t e = cudaMemcpyAsync(graphs.p, h_graphs, sizeof(GraphRef) * (size_t)k, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, sizeof(DevCounters), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(per_vertex.p, 0, sizeof(uint64_t) * (size_t)total, stream);
     if (e == cudaSuccess)
         e = launch_orient_batch((const GraphRef*)graphs.p, k, bits, total, (int32_t*)ws.deg.p, (int32_t*)ws.kept.p,
                                 (long long*)ws.partial.p, (int32_t*)dag_ptr.p, (int32_t*)dag_col.p,
-                                nnz_total / 2 + 1, ctr, ctx->num_sms, stream, &ctx->launches);
+                                nnz_total / 2 + 1, ctr, ctx->num_sms, stream, &nl);
     if (e == cudaSuccess)
         e = launch_bin((const int32_t*)dag_ptr.p, total, ctx->cfg, (int32_t*)ws.warp_list.p, (int2*)ws.warp_desc.p,
                        (int2*)ws.items.p, (int64_t)(ws.items.bytes / sizeof(int2)), ctr, ctx->num_sms, stream,
-                       &ctx->launches);
+                       &nl);
     if (e == cudaSuccess)
         e = launch_count((const int32_t*)dag_ptr.p, (const int32_t*)dag_col.p, total,
                          (const int32_t*)ws.warp_list.p, (const int2*)ws.warp_desc.p, (const int2*)ws.items.p,
-                         (unsigned long long*)per_vertex.p, ctx->cfg, ctr, stream, &ctx->launches);
+                         (unsigned long long*)per_vertex.p, ctx->cfg, ctr, stream, &nl);
     if (e == cudaSuccess) {
         k_segsum<<<k, 256, 0, stream>>>((const unsigned long long*)per_vertex.p, (const GraphRef*)graphs.p,
                                         (unsigned long long*)counts.p);
-        ctx->launches += 1;
+        nl += 1;
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h_counts, counts.p, sizeof(uint64_t) * (size_t)k, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_ctr, ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, stream);
+    enqueued_launches = nl;
     return cuda_status(ctx, e, "batch kernels");
 }
 
 tc_status BatchRunner::launch(tc_ctx* ctx, bool use_graph) {
-    if (!use_graph) return enqueue(ctx);
+    if (!use_graph) {
+        tc_status s = enqueue(ctx);
+        ctx->launches += enqueued_launches;
+        return s;
+    }
     const bool same = exec && !moved && key_k == k && key_total == total && key_nnz == nnz_total &&
                       key_bits == bits && key_cfg == ctx->cfg_version;
     if (!same) {
@@ -180,10 +186,8 @@ tc_status BatchRunner::launch(tc_ctx* ctx, bool use_graph) {
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_status(ctx, e, "cudaStreamBeginCapture");
-        const long long before = ctx->launches;
         tc_status s = enqueue(ctx);
-        captured_launches = ctx->launches - before;  // recorded, not yet run
-        ctx->launches = before;
+        captured_launches = enqueued_launches;  // recorded in the graph, run at each replay
         e = cudaStreamEndCapture(stream, &g);
         if (s) {
             if (g) cudaGraphDestroy(g);
