@@ -193,16 +193,21 @@ void worker_loop(tc_ctx* ctx) {
         bool launched = false;
         for (Round& r : S.rounds) {
             if (r.busy || S.admitted.empty()) continue;
+            // a round holds requests of one offset width, oldest first
+            const int bits = S.admitted.front()->bits;
             long long entries = 0;
-            size_t take = 0;
-            while (take < S.admitted.size() && (int)take < kMaxRoundGraphs) {
-                const long long e2 = entries + S.admitted[take]->nnz + S.admitted[take]->n;
-                if (take > 0 && e2 > kMaxRoundEntries) break;
+            r.reqs.clear();
+            for (size_t i = 0; i < S.admitted.size() && (int)r.reqs.size() < kMaxRoundGraphs;) {
+                Request* q = S.admitted[i];
+                const long long e2 = entries + q->nnz + q->n;
+                if (q->bits != bits || (!r.reqs.empty() && e2 > kMaxRoundEntries)) {
+                    ++i;
+                    continue;
+                }
                 entries = e2;
-                ++take;
+                r.reqs.push_back(q);
+                S.admitted.erase(S.admitted.begin() + (long)i);
             }
-            r.reqs.assign(S.admitted.begin(), S.admitted.begin() + take);
-            S.admitted.erase(S.admitted.begin(), S.admitted.begin() + take);
             for (Request* q : r.reqs) q->state = ReqState::Running;
             r.busy = true;
             lk.unlock();
