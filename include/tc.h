@@ -91,22 +91,24 @@ typedef struct {
 } tc_dag;
 
 /* Tunables. Zero in any field means "use the default" (tc_default_params).
- * The paper's constants are noted beside each (Sec. 3.1, 3.2, 4.3). */
+ * The paper's constants are noted beside each (Sec. 3.1, 3.2, 4.3). Every
+ * table bucket holds 4 keys (the paper's maximum collision count is 128 with
+ * 6 levels cached in shared memory); a fuller bucket overflows to the next. */
 typedef struct {
     int32_t warp_max_out_degree; /* d+ above this -> thread-block worker, <= 255 (paper: 100; default 128) */
     int32_t warp_area_ints;      /* shared-memory table area of one warp worker, ints (default 1088);
                                     a warp-worker table has B = 2*nextpow2(d+) buckets of 4 slots */
     int32_t warp_min_buckets;    /* fewest buckets of a warp-worker table, power of two >= 16 (default 16) */
-    int32_t max_levels;          /* cap on the levels of a thread-block table (paper's max collision: 128) */
     int32_t block_threads;       /* threads of a thread-block worker (default 1024) */
     int32_t block_smem_bytes;    /* shared memory of a thread-block worker (default 200 KiB) */
-    int32_t item_neighbors;      /* out-neighbours of a large vertex per work item (default 1024) */
+    int32_t item_neighbors;      /* out-neighbours of a large vertex per work item, <= block_threads (default 1024) */
     int32_t chunk;               /* vertices a warp takes per queue pop, 1..32 (Sec. 4.3; paper: 1..7; default 32) */
     int32_t warps_per_block;     /* warps per block of the warp-worker kernel (default 8) */
     int32_t shard_count;         /* workload partition (Sec. 5.1): count only u with */
     int32_t shard_index;         /*   u % shard_count == shard_index (default 1 / 0) */
     int32_t validate;            /* reserved for extra input checks (0) */
     int32_t record_timing;       /* 1: record CUDA events around the kernel phases (tc_read_timing) */
+    int32_t hash_mode;           /* 0: multiplicative hashing (default); 1: x mod B, Algorithm 1's hash */
     int32_t reserved[3];
 } tc_params;
 

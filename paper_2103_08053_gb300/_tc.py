@@ -48,10 +48,10 @@ class tc_dag(ctypes.Structure):
 
 class tc_params(ctypes.Structure):
     _fields_ = [("warp_max_out_degree", c_int32), ("warp_area_ints", c_int32), ("warp_min_buckets", c_int32),
-                ("max_levels", c_int32), ("block_threads", c_int32), ("block_smem_bytes", c_int32),
+                ("block_threads", c_int32), ("block_smem_bytes", c_int32),
                 ("item_neighbors", c_int32), ("chunk", c_int32), ("warps_per_block", c_int32),
                 ("shard_count", c_int32), ("shard_index", c_int32), ("validate", c_int32),
-                ("record_timing", c_int32), ("reserved", c_int32 * 3)]
+                ("record_timing", c_int32), ("hash_mode", c_int32), ("reserved", c_int32 * 3)]
 
 
 class tc_timing(ctypes.Structure):

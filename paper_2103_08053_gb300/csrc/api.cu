@@ -93,7 +93,6 @@ static void fill_defaults(tc_params* p) {
     p->warp_max_out_degree = 128;
     p->warp_area_ints = 1088;
     p->warp_min_buckets = 16;
-    p->max_levels = 128;
     p->block_threads = 1024;
     p->block_smem_bytes = 200 * 1024;
     p->item_neighbors = 1024;
@@ -117,7 +116,6 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         TAKE(warp_max_out_degree);
         TAKE(warp_area_ints);
         TAKE(warp_min_buckets);
-        TAKE(max_levels);
         TAKE(block_threads);
         TAKE(block_smem_bytes);
         TAKE(item_neighbors);
@@ -127,13 +125,13 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         p.shard_index = in->shard_index;
         p.validate = in->validate;
         p.record_timing = in->record_timing;
+        p.hash_mode = in->hash_mode;
 #undef TAKE
     }
     if (p.warp_max_out_degree < 1 || p.warp_max_out_degree > 255)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "warp_max_out_degree must be in [1, 255]");
     if (!is_pow2(p.warp_min_buckets) || p.warp_min_buckets < 16 || p.warp_min_buckets > 4096)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "warp_min_buckets must be a power of two in [16, 4096]");
-    if (p.max_levels < 2) return ctx_fail(ctx, TC_ERR_INVALID_ARG, "max_levels must be >= 2");
     if (p.warp_area_ints < 16 || p.warp_area_ints % 4)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "warp_area_ints must be a multiple of 4");
     {
@@ -147,8 +145,9 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [64, 1024]");
     if (p.warps_per_block < 1 || p.warps_per_block > 32)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "warps_per_block must be in [1, 32]");
-    if (p.item_neighbors < 32 || p.item_neighbors % 32)
-        return ctx_fail(ctx, TC_ERR_INVALID_ARG, "item_neighbors must be a positive multiple of 32");
+    if (p.item_neighbors < 32 || p.item_neighbors > p.block_threads || p.item_neighbors % 32)
+        return ctx_fail(ctx, TC_ERR_INVALID_ARG, "item_neighbors must be a multiple of 32 in [32, block_threads]");
+    if (p.hash_mode != 0 && p.hash_mode != 1) return ctx_fail(ctx, TC_ERR_INVALID_ARG, "hash_mode must be 0 or 1");
     if (p.chunk < 1 || p.chunk > 32) return ctx_fail(ctx, TC_ERR_INVALID_ARG, "chunk must be in [1, 32]");
     if (p.shard_count < 1 || p.shard_index < 0 || p.shard_index >= p.shard_count)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "need 0 <= shard_index < shard_count");
@@ -159,14 +158,13 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "warp kernel needs %lld B of shared memory (max %d)", warp_smem,
                         max_smem);
     if (p.block_smem_bytes > max_smem || p.block_smem_bytes % 16 ||
-        p.block_smem_bytes / 4 - (p.block_threads / 32) * 160 < 96)
+        p.block_smem_bytes / 4 - (p.block_threads / 32) * 160 - 2 * p.item_neighbors < 5 * 64)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "block_smem_bytes out of range (max %d)", max_smem);
     if (out) *out = p;
     if (cfg) {
         cfg->warp_max_out_degree = p.warp_max_out_degree;
         cfg->warp_area_ints = p.warp_area_ints;
         cfg->warp_min_buckets = p.warp_min_buckets;
-        cfg->max_levels = p.max_levels;
         cfg->warps_per_block = p.warps_per_block;
         cfg->block_threads = p.block_threads;
         cfg->block_smem_bytes = p.block_smem_bytes;
@@ -175,6 +173,7 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         cfg->shard_count = p.shard_count;
         cfg->shard_index = p.shard_index;
         cfg->record_timing = p.record_timing ? 1 : 0;
+        cfg->hash_mode = p.hash_mode;
         cfg->warp_grid = cfg->block_grid = 0;
     }
     return TC_OK;
@@ -210,6 +209,7 @@ tc_status tcg::ensure_orient_ws(tc_ctx* ctx, Workspace& ws, int64_t n, int64_t n
     if ((s = ws.deg.ensure(ctx, (size_t)(n + 1) * 4, st))) return s;
     if ((s = ws.kept.ensure(ctx, (size_t)(n + 1) * 4, st))) return s;
     if ((s = ws.partial.ensure(ctx, (size_t)(scan_blocks(n) + 2) * 8, st))) return s;
+    if ((s = ws.hubs.ensure(ctx, (size_t)(n + 1) * 4, st))) return s;
     return ensure_count_ws(ctx, ws, n, nnz / 2, st);
 }
 
@@ -244,8 +244,8 @@ static tc_status enqueue_orient(tc_ctx* ctx, Workspace& ws, const tc_csr* g, int
     DevCounters* ctr = (DevCounters*)ws.ctr.p;
     long long nl = 0;
     cudaError_t e = launch_orient(g->row_ptr, g->offset_bits, g->col, g->n, g->nnz, (int32_t*)ws.deg.p,
-                                  (int32_t*)ws.kept.p, (long long*)ws.partial.p, dag_ptr, dag_col, cap, ctr,
-                                  ctx->num_sms, st, &nl);
+                                  (int32_t*)ws.kept.p, (long long*)ws.partial.p, dag_ptr, dag_col, cap,
+                                  (int32_t*)ws.hubs.p, ctr, ctx->num_sms, st, &nl);
     ctx->launches += nl;
     if (g->n == 0 && e == cudaSuccess) e = cudaMemsetAsync(dag_ptr, 0, sizeof(int32_t), st);
     return cuda_status(ctx, e, "orientation kernels");

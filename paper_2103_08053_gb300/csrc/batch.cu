@@ -130,6 +130,7 @@ tc_status BatchRunner::prepare(tc_ctx* ctx, const tc_csr* gs, int k) {
     if ((s = ensure_tracked(ctx, ws.deg, (size_t)(total + 1) * 4, stream, mv))) return s;
     if ((s = ensure_tracked(ctx, ws.kept, (size_t)(total + 1) * 4, stream, mv))) return s;
     if ((s = ensure_tracked(ctx, ws.partial, (size_t)(scan_blocks(total) + 2) * 8, stream, mv))) return s;
+    if ((s = ensure_tracked(ctx, ws.hubs, (size_t)(total + 1) * 4, stream, mv))) return s;
     if ((s = ensure_tracked(ctx, ws.warp_list, (size_t)(total + 1) * 4, stream, mv))) return s;
     if ((s = ensure_tracked(ctx, ws.warp_desc, (size_t)(total + 1) * 8, stream, mv))) return s;
     if ((s = ensure_tracked(ctx, ws.items,
@@ -151,7 +152,7 @@ tc_status BatchRunner::enqueue(tc_ctx* ctx) {
     if (e == cudaSuccess)
         e = launch_orient_batch((const GraphRef*)graphs.p, k, bits, total, (int32_t*)ws.deg.p, (int32_t*)ws.kept.p,
                                 (long long*)ws.partial.p, (int32_t*)dag_ptr.p, (int32_t*)dag_col.p,
-                                nnz_total / 2 + 1, ctr, ctx->num_sms, stream, &nl);
+                                nnz_total / 2 + 1, (int32_t*)ws.hubs.p, ctr, ctx->num_sms, stream, &nl);
     if (e == cudaSuccess)
         e = launch_bin((const int32_t*)dag_ptr.p, total, ctx->cfg, (int32_t*)ws.warp_list.p, (int2*)ws.warp_desc.p,
                        (int2*)ws.items.p, (int64_t)(ws.items.bytes / sizeof(int2)), ctr, ctx->num_sms, stream,

@@ -6,7 +6,8 @@
 //   * bucketed table, fixed-size buckets in one contiguous region, slot given
 //     by an atomic increment of the bucket's length (Algorithm 1,
 //     hashTableConstruction; Sec. 3.1);
-//   * hash(x) = x mod B with B a power of two (Algorithm 1, hash);
+//   * hash: multiplicative hashing into B = 2^lgB buckets (Algorithm 1 uses
+//     x mod B; see bucket_of for why the GPU tables do not);
 //   * a bucket that holds its maximum number of elements is full; further keys
 //     go to the next bucket and a search continues through successor buckets
 //     while the bucket it scanned was full (Sec. 3.2, last paragraph: linear
@@ -45,11 +46,13 @@
 // 1 << 8*(h%4) on the word claims a slot of bucket h) and live after the
 // slots: a table is 4B + B/4 ints.
 //
-// Thread-block workers keep the paper's level-major layout (element j of
-// bucket i at j*B + i, lengths in a separate array): B = nextpow2(part),
-// L = min(Lmax, budget/B - 1) >= 2 levels, with N+(u) split into parts of at
-// most P_max (largest power of two with 3*P_max <= budget), each probed by the
-// whole 2-hop list: |N+(u) ∩ N+(v)| = sum over parts of |part ∩ N+(v)|.
+// Thread-block tables use the same bucket-of-4 layout with B = nextpow2(part)
+// buckets (load factor <= 1) and one 32-bit length word per bucket (a bucket
+// of a large table can see more than 255 claims), where N+(u) is split into
+// parts of at most
+// P_max keys (the largest power of two whose table fits the block's shared
+// memory), each probed by the whole 2-hop list:
+// |N+(u) ∩ N+(v)| = sum over parts of |part ∩ N+(v)|.
 #include "tc_internal.h"
 
 namespace tcg {
@@ -63,6 +66,10 @@ static_assert(VC_UNROLL >= 1 && VC_UNROLL <= 4, "VC_UNROLL in [1, 4]");
 
 #ifndef PACK_MIN_BLOCKS
 #define PACK_MIN_BLOCKS 4
+#endif
+
+#ifndef BLOCK_PIECE
+#define BLOCK_PIECE 512  // combined 2-hop indices per piece of a thread-block item
 #endif
 
 constexpr int STAGE_INTS = 160;  // per warp: 4 x 32 compaction lanes | 32 slot hit counters
@@ -97,18 +104,52 @@ __device__ __forceinline__ int vc_owner(int b, int P, int Pex, bool listlane, un
     return j0 + __popc(starts & le) - (int)(starts & 1u);
 }
 
+// ---- bucket hash ----------------------------------------------------------------
+
+// Bucket of key w in a table of 2^lgB buckets: the top lgB bits of w times
+// 2^32/phi (multiplicative hashing). Algorithm 1 hashes x mod B; vertex ids
+// of skewed graphs have biased low bits (an R-MAT id bit is 1 with
+// probability ~0.24), so x mod B crowds a hub's neighbours into few buckets
+// and probes walk long overflow chains -- the collisions the paper reduces by
+// reordering ids (Sec. 4.1). The multiplicative hash spreads any id set
+// evenly; the count does not depend on the hash.
+// HM = 1 selects Algorithm 1's own hash, x mod B.
+template <int HM>
+__device__ __forceinline__ int bucket_of(int w, int lgB) {
+    if (HM == 1) return w & ((1 << lgB) - 1);
+    return (int)(((unsigned)w * 0x9E3779B1u) >> (32 - lgB));
+}
+
 // ---- pack tables (bucket-major, 4 slots, byte lengths) ---------------------
 
 // Algorithm 1 hashTableConstruction, one key: claim a slot of bucket h with
 // an atomic add on its length byte; a full bucket (4 claims) sends the key to
 // the next bucket. sm: shared array; tab/lenw: int offsets of the slots and
-// of the length words; mask = B - 1. Lengths count claims (<= keys <= 255).
-__device__ __forceinline__ void insert_b4(int* sm, int tab, int lenw, int mask, int w) {
-    int h = w & mask;
+// of the length words; B = 2^lgB. Lengths count claims (<= keys <= 255).
+template <int HM>
+__device__ __forceinline__ void insert_b4(int* sm, int tab, int lenw, int lgB, int w) {
+    const int mask = (1 << lgB) - 1;
+    int h = bucket_of<HM>(w, lgB);
     for (int s = 0; s <= mask; ++s) {
         const int sh = 8 * (h & 3);
         const unsigned old = atomicAdd(reinterpret_cast<unsigned*>(sm + lenw + (h >> 2)), 1u << sh);
         const int slot = (old >> sh) & 0xff;
+        if (slot < 4) {
+            sm[tab + 4 * h + slot] = w;
+            return;
+        }
+        h = (h + 1) & mask;
+    }
+}
+
+// Same claim with one 32-bit length word per bucket (thread-block tables,
+// whose buckets can see more than 255 claims).
+template <int HM>
+__device__ __forceinline__ void insert_b4w(int* sm, int tab, int lenw, int lgB, int w) {
+    const int mask = (1 << lgB) - 1;
+    int h = bucket_of<HM>(w, lgB);
+    for (int s = 0; s <= mask; ++s) {
+        const int slot = atomicAdd(sm + lenw + h, 1);
         if (slot < 4) {
             sm[tab + 4 * h + slot] = w;
             return;
@@ -131,26 +172,31 @@ __device__ __noinline__ int probe_b4_chain(const int* sm, int tab, int mask, int
     return 0;
 }
 
-// Probe the 2-hop lists of one chunk of up to 32 out-edges against pack
-// tables. Lane i brings the list N+(v_i) = dag_col[s, s+l) and the table of
-// its edge (tab: int offset of the slots, mask = B-1, slot: pack slot).
-// Empty lists are compacted away (stage: STAGE_INTS ints of smem), the rest
-// are combined virtually and dealt out 32 indices at a time, VC_UNROLL
-// windows per step with all loads of a step issued before its probes. A probe
-// is one 16-byte load and four compares; only a lane whose bucket is full and
-// did not match walks the overflow chain.
-template <bool SLOT_HITS>
-__device__ __forceinline__ uint32_t vc_probe_b4(int s, int l, int tab, int mask, int slot, const int* sm,
-                                                const int32_t* __restrict__ dag_col, int lane, int* stage) {
+// Probe the 2-hop lists of up to 32 out-edges against bucket-of-4 tables.
+// Lane i brings the list N+(v_i) = dag_col[s, s+l) and the table of its edge
+// (tab: int offset of the slots, lgB = log2 B, slot: pack slot). Empty lists
+// are compacted away (stage: STAGE_INTS ints of smem), the rest are combined
+// virtually, and the combined indices [skip, min(limit, total)) are dealt out
+// 32 at a time, VC_UNROLL windows per step with all loads of a step issued
+// before its probes. A probe is one 16-byte load and four compares; only a
+// lane whose bucket is full and did not match walks the overflow chain.
+// Returns the hits; *done = number of combined indices processed.
+template <bool SLOT_HITS, int HM>
+__device__ __forceinline__ uint32_t vc_range_b4(int s, int l, int tab, int lgB, int slot, int skip, int limit,
+                                                const int* sm, const int32_t* __restrict__ dag_col, int lane,
+                                                int* stage, int* done) {
     const unsigned nem = __ballot_sync(FULL, l > 0);
-    if (nem == 0) return 0;
+    if (nem == 0) {
+        *done = 0;
+        return 0;
+    }
     const int c = __popc(nem);
     if (l > 0) {
         const int p = __popc(nem & lanemask_lt(lane));
         stage[p] = s;
         stage[32 + p] = l;
         stage[64 + p] = tab;
-        stage[96 + p] = mask | (slot << 16);
+        stage[96 + p] = lgB | (slot << 16);
     }
     __syncwarp();
     const bool lst = lane < c;
@@ -161,11 +207,12 @@ __device__ __forceinline__ uint32_t vc_probe_b4(int s, int l, int tab, int mask,
     __syncwarp();
     const int P = warp_incl_scan(cl, lane);
     const int total = __shfl_sync(FULL, P, 31);
+    const int end = total < limit ? total : limit;
     const int Pex = P - cl;
-    const int bias = cs - Pex;  // dag_col index of flat position f of this list: bias + f
+    const int bias = cs - Pex;  // dag_col index of combined position f of this list: bias + f
     const unsigned le = lanemask_le(lane);
     uint32_t hits = 0;
-    for (int base = 0; base < total; base += 32 * VC_UNROLL) {
+    for (int base = skip; base < end; base += 32 * VC_UNROLL) {
         int key[VC_UNROLL], kt[VC_UNROLL], km[VC_UNROLL];
 #pragma unroll
         for (int q = 0; q < VC_UNROLL; ++q) {
@@ -175,96 +222,31 @@ __device__ __forceinline__ uint32_t vc_probe_b4(int s, int l, int tab, int mask,
             kt[q] = __shfl_sync(FULL, ctab, o);
             km[q] = __shfl_sync(FULL, cms, o);
             const int f = b + lane;
-            key[q] = (f < total) ? __ldg(dag_col + bo + f) : NOKEY;
+            key[q] = (f < end) ? __ldg(dag_col + bo + f) : NOKEY;
         }
 #pragma unroll
         for (int q = 0; q < VC_UNROLL; ++q) {
-            const int mask = km[q] & 0xffff;
-            const int h = key[q] & mask;
+            const int lg = km[q] & 0xffff;
+            const int h = bucket_of<HM>(key[q], lg);
             const int4 b4 = *reinterpret_cast<const int4*>(sm + kt[q] + 4 * h);
             int hit = match4(b4, key[q]);
             const bool more = key[q] >= 0 && !hit && b4.w != EMPTY;
             if (__any_sync(FULL, more)) {
-                if (more) hit = probe_b4_chain(sm, kt[q], mask, h, key[q]);
+                if (more) hit = probe_b4_chain(sm, kt[q], (1 << lg) - 1, h, key[q]);
             }
             hits += hit;
             if (SLOT_HITS && hit) atomicAdd(&stage[128 + (km[q] >> 16)], 1);
         }
     }
+    *done = end > skip ? end - skip : 0;
     return hits;
 }
 
-// ---- thread-block tables (level-major, L levels) ----------------------------
-
-// Algorithm 1 hashTableConstruction, one key. len[h] starts at EMPTY (-1),
-// so atomicAdd(len[h], 1) + 1 is the claimed level; a full bucket (level >=
-// L) sends the key to the next bucket. Levels never written stay EMPTY, so a
-// search stops at the first empty level without reading len.
-__device__ __forceinline__ void insert_lm(int* len, int* tab, int B, int L, int w) {
-    int h = w & (B - 1);
-    for (int s = 0; s < B; ++s) {
-        const int slot = atomicAdd(&len[h], 1) + 1;
-        if (slot < L) {
-            tab[slot * B + h] = w;
-            return;
-        }
-        h = (h + 1) & (B - 1);
-    }
-}
-
-// Algorithm 1 linearSearch over the levels of bucket hash(w), then of its
-// successors while the scanned bucket was full.
-__device__ __forceinline__ int probe_lm(const int* tab, int B, int L, int w) {
-    int h = w & (B - 1);
-    for (int s = 0; s < B; ++s) {
-        for (int j = 0; j < L; ++j) {
-            const int x = tab[j * B + h];
-            if (x == w) return 1;
-            if (x == EMPTY) return 0;
-        }
-        h = (h + 1) & (B - 1);
-    }
-    return 0;
-}
-
-// Same virtual combination as vc_probe_b4, all lists probed against one
-// level-major table.
-__device__ __forceinline__ uint32_t vc_probe_lm(int s, int l, const int* tab, int B, int L,
+template <bool SLOT_HITS, int HM>
+__device__ __forceinline__ uint32_t vc_probe_b4(int s, int l, int tab, int lgB, int slot, const int* sm,
                                                 const int32_t* __restrict__ dag_col, int lane, int* stage) {
-    const unsigned nem = __ballot_sync(FULL, l > 0);
-    if (nem == 0) return 0;
-    const int c = __popc(nem);
-    if (l > 0) {
-        const int p = __popc(nem & lanemask_lt(lane));
-        stage[p] = s;
-        stage[32 + p] = l;
-    }
-    __syncwarp();
-    const bool lst = lane < c;
-    const int cs = lst ? stage[lane] : 0;
-    const int cl = lst ? stage[32 + lane] : 0;
-    __syncwarp();
-    const int P = warp_incl_scan(cl, lane);
-    const int total = __shfl_sync(FULL, P, 31);
-    const int Pex = P - cl;
-    const int bias = cs - Pex;
-    const unsigned le = lanemask_le(lane);
-    uint32_t hits = 0;
-    for (int base = 0; base < total; base += 32 * VC_UNROLL) {
-        int key[VC_UNROLL];
-#pragma unroll
-        for (int q = 0; q < VC_UNROLL; ++q) {
-            const int b = base + 32 * q;
-            const int o = vc_owner(b, P, Pex, lst, le) & 31;
-            const int bo = __shfl_sync(FULL, bias, o);
-            const int f = b + lane;
-            key[q] = (f < total) ? __ldg(dag_col + bo + f) : NOKEY;
-        }
-#pragma unroll
-        for (int q = 0; q < VC_UNROLL; ++q)
-            if (key[q] >= 0) hits += probe_lm(tab, B, L, key[q]);
-    }
-    return hits;
+    int done;
+    return vc_range_b4<SLOT_HITS, HM>(s, l, tab, lgB, slot, 0, 0x7fffffff, sm, dag_col, lane, stage, &done);
 }
 
 // ---- workers -----------------------------------------------------------------
@@ -307,7 +289,7 @@ __device__ __forceinline__ void list_bounds(int v, const int32_t* __restrict__ d
 // smem per warp: area[area_ints] | stage[STAGE_INTS]. desc[i] = (first
 // out-edge, d+) of warp_list[i]. A pack's area holds all its tables' slots
 // first, then all their length words.
-template <bool PER_VERTEX>
+template <bool PER_VERTEX, int HM>
 __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
     k_count_pack(const int32_t* __restrict__ dag_ptr, const int32_t* __restrict__ dag_col,
                  const int2* __restrict__ desc, const int32_t* __restrict__ warp_list,
@@ -373,8 +355,8 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
                 for (int q = 0; q < VC_UNROLL; ++q) {
                     const int tb = __shfl_sync(FULL, my_tab, own[q]);
                     const int lw = __shfl_sync(FULL, my_len, own[q]);
-                    const int mk = __shfl_sync(FULL, B, own[q]) - 1;
-                    if (key[q] >= 0) insert_b4(smem, tb, lw, mk, key[q]);
+                    const int lg = __shfl_sync(FULL, lgB, own[q]);
+                    if (key[q] >= 0) insert_b4<HM>(smem, tb, lw, lg, key[q]);
                 }
             }
             __syncwarp();
@@ -385,7 +367,7 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
                 const int o = vc_owner(0, K, Kex, true, le) & 31;
                 const int bo = __shfl_sync(FULL, kbias, o);
                 etab = __shfl_sync(FULL, my_tab, o);
-                emask = __shfl_sync(FULL, B, o) - 1;
+                emask = __shfl_sync(FULL, lgB, o);
                 eslot = o;
                 list_bounds(lane < E ? __ldg(dag_col + bo + lane) : -1, dag_ptr, n, ctr, s, l);
             }
@@ -395,12 +377,12 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
                     const int o = vc_owner(c0 + 32, K, Kex, true, le) & 31;
                     const int bo = __shfl_sync(FULL, kbias, o);
                     ntab = __shfl_sync(FULL, my_tab, o);
-                    nmask = __shfl_sync(FULL, B, o) - 1;
+                    nmask = __shfl_sync(FULL, lgB, o);
                     nslot = o;
                     const int e = c0 + 32 + lane;
                     list_bounds(e < E ? __ldg(dag_col + bo + e) : -1, dag_ptr, n, ctr, ns, nl);
                 }
-                hits += vc_probe_b4<PER_VERTEX>(s, l, etab, emask, eslot, smem, dag_col, lane, stage);
+                hits += vc_probe_b4<PER_VERTEX, HM>(s, l, etab, emask, eslot, smem, dag_col, lane, stage);
                 s = ns;
                 l = nl;
                 etab = ntab;
@@ -419,19 +401,28 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
     block_add_total(acc, ctr);
 }
 
-// Thread-block workers: one block per work item (u, first neighbour) of a
-// vertex with d+ > T_w. smem: stage[nwarps * STAGE_INTS] | len[B] | tab[B*L].
-// Warp w of the block takes the item's 32-neighbour chunks w, w + nw, ...
+// Thread-block workers: one block per work item (u, out-neighbours
+// [nb0, nb1)) of a vertex with d+ > T_w; nb1 - nb0 <= item_nbrs <= 1024.
+// smem: stage[nwarps * STAGE_INTS] | S[item_nbrs] | LP[item_nbrs] | table.
+// The block loads the item's out-neighbours' list bounds (S = starts, LP =
+// inclusive prefix of lengths) once, builds the table of one part of N+(u),
+// and its warps take pieces of PIECE combined 2-hop indices from a shared
+// counter: a warp finds the list holding its piece's first index by a
+// two-round 32-ary search of LP, then probes the piece with the virtual
+// combination of the next 32 lists (more rounds if the piece spans more).
+template <int PIECE, int HM>
 __global__ void __launch_bounds__(1024, 1)
     k_count_block(const int32_t* __restrict__ dag_ptr, const int32_t* __restrict__ dag_col,
                   const int2* __restrict__ items, unsigned long long* __restrict__ per_vertex, DevCounters* ctr,
-                  int n, int budget_ints, int part_max, int max_levels, int item_nbrs) {
+                  int n, int table_off, int part_max, int item_nbrs) {
     extern __shared__ int smem[];
-    __shared__ int s_item;
+    __shared__ int s_item, s_piece;
+    __shared__ int s_wsum[32];
     if (ctr->err) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int* stage = smem + w * STAGE_INTS;
-    int* area = smem + nw * STAGE_INTS;
+    int* S = smem + nw * STAGE_INTS;
+    int* LP = S + item_nbrs;
     const int nitems = ctr->n_items;
     unsigned long long acc = 0;
     for (;;) {
@@ -444,29 +435,61 @@ __global__ void __launch_bounds__(1024, 1)
         const int u = item.x;
         const int a = dag_ptr[u];
         const int k = dag_ptr[u + 1] - a;
-        const int nb0 = item.y, nb1 = min(k, nb0 + item_nbrs);
+        const int nb0 = item.y, cnt = min(k, nb0 + item_nbrs) - nb0;
+        // list bounds of the item's out-neighbours, and the block-wide prefix of their lengths
+        int ls = 0, ll = 0;
+        if ((int)threadIdx.x < cnt) list_bounds(__ldg(dag_col + a + nb0 + threadIdx.x), dag_ptr, n, ctr, ls, ll);
+        const int wi = warp_incl_scan(ll, lane);
+        if (lane == 31) s_wsum[w] = wi;
+        __syncthreads();
+        if (w == 0) {
+            const int x = lane < nw ? s_wsum[lane] : 0;
+            s_wsum[lane] = warp_incl_scan(x, lane) - x;
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < cnt) {
+            S[threadIdx.x] = ls;
+            LP[threadIdx.x] = s_wsum[w] + wi;
+        }
+        __syncthreads();
+        const int W = cnt > 0 ? LP[cnt - 1] : 0;
         uint32_t h = 0;
-        for (int p0 = 0; p0 < k; p0 += part_max) {
+        for (int p0 = 0; p0 < k && W > 0; p0 += part_max) {
             const int pk = min(part_max, k - p0);
             const int B = next_pow2(pk < 32 ? 32 : pk);
-            int L = budget_ints / B - 1;
-            L = L < max_levels ? L : max_levels;
-            for (int t = threadIdx.x; t < B * (L + 1); t += blockDim.x) area[t] = EMPTY;
+            const int lgB = 31 - __clz(B);
+            int* tab = smem + table_off;
+            const int lenw = table_off + 4 * B;
+            for (int t = threadIdx.x * 4; t < 4 * B; t += blockDim.x * 4)
+                *reinterpret_cast<int4*>(tab + t) = make_int4(EMPTY, EMPTY, EMPTY, EMPTY);
+            for (int t = threadIdx.x; t < B; t += blockDim.x) smem[lenw + t] = 0;
+            if (threadIdx.x == 0) s_piece = 0;
             __syncthreads();
             for (int t = threadIdx.x; t < pk; t += blockDim.x)
-                insert_lm(area, area + B, B, L, __ldg(dag_col + a + p0 + t));
+                insert_b4w<HM>(smem, table_off, lenw, lgB, __ldg(dag_col + a + p0 + t));
             __syncthreads();
-            int c0 = nb0 + 32 * w;
-            int s = 0, l = 0;
-            if (c0 < nb1) list_bounds(c0 + lane < nb1 ? __ldg(dag_col + a + c0 + lane) : -1, dag_ptr, n, ctr, s, l);
-            for (; c0 < nb1; c0 += 32 * nw) {
-                const int c1 = c0 + 32 * nw;
-                int ns = 0, nl = 0;
-                if (c1 < nb1)
-                    list_bounds(c1 + lane < nb1 ? __ldg(dag_col + a + c1 + lane) : -1, dag_ptr, n, ctr, ns, nl);
-                h += vc_probe_lm(s, l, area + B, B, L, dag_col, lane, stage);
-                s = ns;
-                l = nl;
+            for (;;) {
+                int pc = 0;
+                if (lane == 0) pc = atomicAdd(&s_piece, 1);
+                pc = __shfl_sync(FULL, pc, 0);
+                int F = pc * PIECE;
+                if (F >= W) break;
+                const int F1 = min(W, F + PIECE);
+                while (F < F1) {
+                    // j0 = first list with LP[j0] > F (cnt <= 1024: two 32-ary rounds)
+                    const int i1 = min(cnt - 1, lane * 32 + 31);
+                    const int blk = __popc(__ballot_sync(FULL, lane * 32 < cnt && LP[i1] <= F));
+                    const int i2 = blk * 32 + lane;
+                    const int j0 = blk * 32 + __popc(__ballot_sync(FULL, i2 < cnt && LP[i2] <= F));
+                    const int j = j0 + lane;
+                    const int lj = j < cnt ? LP[j] - (j ? LP[j - 1] : 0) : 0;
+                    const int sj = j < cnt ? S[j] : 0;
+                    const int base_flat = j0 ? LP[j0 - 1] : 0;
+                    int done = 0;
+                    h += vc_range_b4<false, HM>(sj, lj, table_off, lgB, 0, F - base_flat, F1 - base_flat, smem,
+                                            dag_col, lane, stage, &done);
+                    F += done;
+                }
             }
             __syncthreads();
         }
@@ -533,7 +556,15 @@ int pack_smem_bytes(const CountCfg& cfg) { return cfg.warps_per_block * (cfg.war
 using PackKernel = void (*)(const int32_t*, const int32_t*, const int2*, const int32_t*, unsigned long long*,
                             DevCounters*, int, int, int, int);
 
-PackKernel pack_kernel(bool per_vertex) { return per_vertex ? k_count_pack<true> : k_count_pack<false>; }
+PackKernel pack_kernel(bool per_vertex, int hm) {
+    if (hm == 1) return per_vertex ? k_count_pack<true, 1> : k_count_pack<false, 1>;
+    return per_vertex ? k_count_pack<true, 0> : k_count_pack<false, 0>;
+}
+
+using BlockKernel = void (*)(const int32_t*, const int32_t*, const int2*, unsigned long long*, DevCounters*, int,
+                             int, int, int);
+
+BlockKernel block_kernel(int hm) { return hm == 1 ? k_count_block<BLOCK_PIECE, 1> : k_count_block<BLOCK_PIECE, 0>; }
 
 int lg2(int x) {
     int l = 0;
@@ -549,24 +580,39 @@ int pack_table_ints(int max_out_degree, int min_buckets) {
     return 4 * b + b / 4;
 }
 
+// Shared-memory ints a thread-block worker has for its table, after the
+// warps' stages and the item's list bounds and prefix.
 int count_block_budget_ints(const CountCfg& cfg) {
-    return cfg.block_smem_bytes / 4 - (cfg.block_threads / 32) * STAGE_INTS;
+    return cfg.block_smem_bytes / 4 - (cfg.block_threads / 32) * STAGE_INTS - 2 * cfg.item_neighbors;
+}
+
+// Largest part of N+(u) whose bucket-of-4 table (B = nextpow2(part) buckets,
+// 4B slots + B length words) fits the budget.
+int count_block_part_max(const CountCfg& cfg) {
+    const int budget = count_block_budget_ints(cfg);
+    int p = 32;
+    while (5 * (2 * p) <= budget) p *= 2;
+    return p;
 }
 
 cudaError_t count_kernel_setup(CountCfg& cfg, int num_sms) {
     const int warp_smem = pack_smem_bytes(cfg);
     cudaError_t e = cudaSuccess;
     for (int pv = 0; pv < 2 && e == cudaSuccess; ++pv)
-        e = cudaFuncSetAttribute(pack_kernel(pv), cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem);
+        e = cudaFuncSetAttribute(pack_kernel(pv, cfg.hash_mode), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 warp_smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_count_block, cudaFuncAttributeMaxDynamicSharedMemorySize, cfg.block_smem_bytes);
+    e = cudaFuncSetAttribute(block_kernel(cfg.hash_mode), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             cfg.block_smem_bytes);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pack_kernel(false), cfg.warps_per_block * 32,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pack_kernel(false, cfg.hash_mode),
+                                                      cfg.warps_per_block * 32,
                                                       warp_smem);
     if (e != cudaSuccess) return e;
     cfg.warp_grid = num_sms * (per_sm > 0 ? per_sm : 1);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_block, cfg.block_threads, cfg.block_smem_bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, block_kernel(cfg.hash_mode), cfg.block_threads,
+                                                      cfg.block_smem_bytes);
     if (e != cudaSuccess) return e;
     cfg.block_grid = num_sms * (per_sm > 0 ? per_sm : 1);
     return cudaSuccess;
@@ -576,12 +622,11 @@ cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t
                          const int2* warp_desc, const int2* items, unsigned long long* per_vertex,
                          const CountCfg& cfg, DevCounters* ctr, cudaStream_t st, long long* launches) {
     *launches += 2;
-    const int budget = count_block_budget_ints(cfg);
-    int part_max = 1;
-    while (part_max * 2 * 3 <= budget) part_max *= 2;
-    k_count_block<<<cfg.block_grid, cfg.block_threads, cfg.block_smem_bytes, st>>>(
-        dag_ptr, dag_col, items, per_vertex, ctr, (int)n, budget, part_max, cfg.max_levels, cfg.item_neighbors);
-    pack_kernel(per_vertex != nullptr)<<<cfg.warp_grid, cfg.warps_per_block * 32, pack_smem_bytes(cfg), st>>>(
+    const int table_off = (cfg.block_threads / 32) * STAGE_INTS + 2 * cfg.item_neighbors;
+    block_kernel(cfg.hash_mode)<<<cfg.block_grid, cfg.block_threads, cfg.block_smem_bytes, st>>>(
+        dag_ptr, dag_col, items, per_vertex, ctr, (int)n, table_off, count_block_part_max(cfg), cfg.item_neighbors);
+    pack_kernel(per_vertex != nullptr, cfg.hash_mode)<<<cfg.warp_grid, cfg.warps_per_block * 32,
+                                                      pack_smem_bytes(cfg), st>>>(
         dag_ptr, dag_col, warp_desc, warp_list, per_vertex, ctr, (int)n, cfg.warp_area_ints,
         lg2(cfg.warp_min_buckets), cfg.chunk);
     return cudaGetLastError();

@@ -45,7 +45,7 @@ __device__ __forceinline__ GraphRef graph_of(int64_t row, const GraphRef& one, c
 
 template <typename Off, bool BATCH>
 __global__ void k_degree(GraphRef one, const GraphRef* __restrict__ gs, int k, int64_t total,
-                         int32_t* __restrict__ deg, DevCounters* ctr) {
+                         int32_t* __restrict__ deg, int32_t* __restrict__ hubs, DevCounters* ctr) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < total; u += stride) {
         const GraphRef G = graph_of<BATCH>(u, one, gs, k);
@@ -61,6 +61,7 @@ __global__ void k_degree(GraphRef one, const GraphRef* __restrict__ gs, int k, i
             }
         }
         deg[u] = (int32_t)d;
+        if (d > HUB_DEGREE) hubs[atomicAdd(&ctr->n_hub, 1)] = (int32_t)u;
     }
 }
 
@@ -78,6 +79,7 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
              int32_t* __restrict__ kept, const int32_t* __restrict__ dag_ptr, int32_t* __restrict__ dag_col,
              int64_t dag_cap, DevCounters* ctr) {
     __shared__ long long s_st[ORIENT_WARPS][33];
+    __shared__ long long s_as[ORIENT_WARPS][32];
     __shared__ int s_cnt[ORIENT_WARPS][32];
     __shared__ int s_dp[ORIENT_WARPS][32];
     if (COMPACT && ctr->err) return;
@@ -85,6 +87,7 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
     const unsigned le = lanemask_le(lane), lt = lanemask_lt(lane);
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     long long* st = s_st[w];
+    long long* as = s_as[w];
     int* cnt = s_cnt[w];
     int* dp = s_dp[w];
     for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g * 32 < total; g += nw) {
@@ -109,12 +112,22 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
             if (lane == 0) atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
             continue;
         }
-        st[lane] = a;
-        if (lane == 0) st[32] = e;
+        // hub rows (left to the hub kernel) take no room in the warp's walk:
+        // st holds virtual starts over the other rows, as their real starts
+        const long long len = (lane < nr && nx - a <= HUB_DEGREE) ? nx - a : 0;
+        long long vin = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long t = __shfl_up_sync(FULL, vin, o);
+            if (lane >= o) vin += t;
+        }
+        st[lane] = vin - len;
+        as[lane] = a;
+        if (lane == 31) st[32] = vin;
         cnt[lane] = 0;
         if (COMPACT) dp[lane] = (lane < nr) ? dag_ptr[g * 32 + lane] : 0;
         __syncwarp();
-        const long long gb = __shfl_sync(FULL, a, 0), ge = e;
+        const long long gb = 0, ge = st[32];
         int r = 0;
         for (long long base = gb; base < ge; base += 32 * ORIENT_UNROLL) {
             // issue every load of the step first: ORIENT_UNROLL col reads, then
@@ -123,7 +136,10 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
 #pragma unroll
             for (int q = 0; q < ORIENT_UNROLL; ++q) {
                 const long long f = base + 32 * q + lane;
-                vq[q] = (f < ge) ? __ldg(col + f) : -1;
+                int rq = r;
+                if (f < ge)
+                    while (st[rq + 1] <= f) ++rq;
+                vq[q] = (f < ge) ? __ldg(col + as[rq] + (f - st[rq])) : -1;
             }
 #pragma unroll
             for (int q = 0; q < ORIENT_UNROLL; ++q)
@@ -139,7 +155,7 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
                     if ((unsigned)v >= (unsigned long long)n) {
                         atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
                     } else {
-                        const int du = (int)(st[r + 1] - st[r]);
+                        const int du = deg[vb + u0 + r];
                         const int dv = dq[q];
                         keep = (dv > du) || (dv == du && (int64_t)v > u0 + r);
                     }
@@ -176,6 +192,111 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
                 kept[u0 + lane] = cnt[lane];
         }
         __syncwarp();
+    }
+}
+
+// Orientation of hub rows (degree > HUB_DEGREE): one block per row, rows
+// taken from the hub list with an atomic cursor. A tile is 4 consecutive
+// entries per thread (loads issued together); the count pass reduces the
+// kept entries of the row, the compaction pass places them in input order
+// with a block-wide exclusive scan per tile.
+constexpr int HUB_THREADS = 512;
+
+template <typename Off, bool COMPACT, bool BATCH>
+__global__ void __launch_bounds__(HUB_THREADS)
+    k_orient_hub(GraphRef one, const GraphRef* __restrict__ gs, int k, const int32_t* __restrict__ hubs,
+                 const int32_t* __restrict__ deg, int32_t* __restrict__ kept, const int32_t* __restrict__ dag_ptr,
+                 int32_t* __restrict__ dag_col, int64_t dag_cap, DevCounters* ctr) {
+    __shared__ int s_row, s_carry;
+    __shared__ int s_w[HUB_THREADS / 32];
+    if (COMPACT && ctr->err) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = HUB_THREADS / 32;
+    const int nh = ctr->n_hub;
+    for (;;) {
+        if (threadIdx.x == 0) s_row = atomicAdd(&ctr->q_hub[COMPACT ? 1 : 0], 1);
+        __syncthreads();
+        const int hi = s_row;
+        if (hi >= nh) break;
+        const int64_t ug = hubs[hi];
+        const GraphRef G = graph_of<BATCH>(ug, one, gs, k);
+        const int64_t u = ug - G.vbase;
+        const Off* rp = static_cast<const Off*>(G.row_ptr);
+        const long long a = (long long)rp[u], b = (long long)rp[u + 1];  // checked by k_degree
+        const int du = deg[ug];
+        if (threadIdx.x == 0) s_carry = 0;
+        __syncthreads();
+        long long pos0 = COMPACT ? (long long)dag_ptr[ug] : 0;
+        int total = 0;
+        for (long long t0 = a; t0 < b; t0 += 4LL * HUB_THREADS) {
+            const long long e0 = t0 + 4LL * threadIdx.x;
+            int v[4], keepc = 0;
+            bool kq[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = (e0 + q < b) ? __ldg(G.col + e0 + q) : -1;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                kq[q] = false;
+                if (e0 + q < b) {
+                    if ((unsigned)v[q] >= (unsigned long long)G.n) {
+                        atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
+                    } else {
+                        const int dv = __ldg(deg + G.vbase + v[q]);
+                        kq[q] = (dv > du) || (dv == du && (int64_t)v[q] > u);
+                    }
+                }
+                keepc += kq[q];
+            }
+            if (!COMPACT) {
+                total += keepc;
+                continue;
+            }
+            // exclusive block scan of keepc
+            int inc = keepc;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(FULL, inc, o);
+                if (lane >= o) inc += t;
+            }
+            if (lane == 31) s_w[w] = inc;
+            __syncthreads();
+            if (w == 0) {
+                const int x = lane < nw ? s_w[lane] : 0;
+                int xi = x;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(FULL, xi, o);
+                    if (lane >= o) xi += t;
+                }
+                if (lane < nw) s_w[lane] = xi - x;
+            }
+            __syncthreads();
+            long long p = pos0 + s_carry + s_w[w] + inc - keepc;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (kq[q]) {
+                    if (p < dag_cap)
+                        dag_col[p] = (int32_t)(G.vbase + v[q]);
+                    else
+                        atomicOr(&ctr->err, ERRBIT_DAG_OVERFLOW);
+                    ++p;
+                }
+            __syncthreads();
+            if (threadIdx.x == HUB_THREADS - 1) s_carry += s_w[w] + inc;
+            __syncthreads();
+        }
+        if (!COMPACT) {
+            // block sum of the kept entries -> kept[ug]
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(FULL, total, o);
+            if (lane == 0) s_w[w] = total;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int t = 0;
+                for (int i = 0; i < nw; ++i) t += s_w[i];
+                kept[ug] = t;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -322,25 +443,30 @@ __global__ void k_bin(const int32_t* __restrict__ dag_ptr, int64_t n, int warp_m
 
 template <typename Off, bool BATCH>
 cudaError_t orient_t(const GraphRef& one, const GraphRef* gs, int k, int64_t total, int32_t* deg, int32_t* kept,
-                     long long* partial, int32_t* dag_ptr, int32_t* dag_col, int64_t dag_cap, DevCounters* ctr,
-                     int num_sms, cudaStream_t st, long long* launches) {
+                     long long* partial, int32_t* dag_ptr, int32_t* dag_col, int64_t dag_cap, int32_t* hubs,
+                     DevCounters* ctr, int num_sms, cudaStream_t st, long long* launches) {
     if (total <= 0) return cudaSuccess;
-    *launches += 6;
+    *launches += 8;
+    const int hg = num_sms * 2;
     const int64_t groups = (total + 31) / 32;
     int og = (int)((groups + ORIENT_WARPS - 1) / ORIENT_WARPS);
     const int og_cap = num_sms * 8 * 4;
     if (og > og_cap) og = og_cap;
     int dg = (int)((total + 255) / 256);
     if (dg > num_sms * 16) dg = num_sms * 16;
-    k_degree<Off, BATCH><<<dg, 256, 0, st>>>(one, gs, k, total, deg, ctr);
+    k_degree<Off, BATCH><<<dg, 256, 0, st>>>(one, gs, k, total, deg, hubs, ctr);
     k_orient<Off, false, BATCH><<<og, ORIENT_THREADS, 0, st>>>(one, gs, k, total, deg, kept, nullptr, nullptr, 0,
                                                                 ctr);
+    k_orient_hub<Off, false, BATCH><<<hg, HUB_THREADS, 0, st>>>(one, gs, k, hubs, deg, kept, nullptr, nullptr, 0,
+                                                                 ctr);
     const int nb = scan_blocks(total);
     k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(kept, total, partial);
     k_scan_top<<<1, SCAN_TOP_THREADS, 0, st>>>(partial, nb, dag_ptr, total, ctr);
     k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(kept, total, partial, dag_ptr);
     k_orient<Off, true, BATCH><<<og, ORIENT_THREADS, 0, st>>>(one, gs, k, total, deg, nullptr, dag_ptr, dag_col,
                                                                dag_cap, ctr);
+    k_orient_hub<Off, true, BATCH><<<hg, HUB_THREADS, 0, st>>>(one, gs, k, hubs, deg, nullptr, dag_ptr, dag_col,
+                                                                dag_cap, ctr);
     return cudaGetLastError();
 }
 
@@ -350,24 +476,25 @@ int scan_blocks(int64_t n) { return (int)((n + SCAN_TILE - 1) / SCAN_TILE); }
 
 cudaError_t launch_orient(const void* row_ptr, int offset_bits, const int32_t* col, int64_t n, int64_t nnz,
                           int32_t* deg, int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
-                          int64_t dag_cap, DevCounters* ctr, int num_sms, cudaStream_t st, long long* launches) {
+                          int64_t dag_cap, int32_t* hubs, DevCounters* ctr, int num_sms, cudaStream_t st,
+                          long long* launches) {
     const GraphRef one{row_ptr, col, n, nnz, 0};
     if (offset_bits == 64)
-        return orient_t<long long, false>(one, nullptr, 1, n, deg, kept, partial, dag_ptr, dag_col, dag_cap, ctr,
-                                          num_sms, st, launches);
-    return orient_t<int32_t, false>(one, nullptr, 1, n, deg, kept, partial, dag_ptr, dag_col, dag_cap, ctr, num_sms,
-                                    st, launches);
+        return orient_t<long long, false>(one, nullptr, 1, n, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs,
+                                          ctr, num_sms, st, launches);
+    return orient_t<int32_t, false>(one, nullptr, 1, n, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs, ctr,
+                                    num_sms, st, launches);
 }
 
 cudaError_t launch_orient_batch(const GraphRef* graphs, int k, int offset_bits, int64_t total, int32_t* deg,
                                 int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
-                                int64_t dag_cap, DevCounters* ctr, int num_sms, cudaStream_t st,
+                                int64_t dag_cap, int32_t* hubs, DevCounters* ctr, int num_sms, cudaStream_t st,
                                 long long* launches) {
     const GraphRef none{nullptr, nullptr, 0, 0, 0};
     if (offset_bits == 64)
-        return orient_t<long long, true>(none, graphs, k, total, deg, kept, partial, dag_ptr, dag_col, dag_cap, ctr,
-                                         num_sms, st, launches);
-    return orient_t<int32_t, true>(none, graphs, k, total, deg, kept, partial, dag_ptr, dag_col, dag_cap, ctr,
+        return orient_t<long long, true>(none, graphs, k, total, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs,
+                                         ctr, num_sms, st, launches);
+    return orient_t<int32_t, true>(none, graphs, k, total, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs, ctr,
                                    num_sms, st, launches);
 }
 

@@ -28,7 +28,9 @@ struct DevCounters {
     int q_warp;                // queue cursors (atomic chunk pops, Sec. 4.3)
     int q_items;
     int err;                   // ERRBIT_* flags
-    int pad[6];
+    int n_hub;                 // rows with degree > HUB_DEGREE (orientation by thread blocks)
+    int q_hub[2];              // hub-row cursors of the two orientation passes
+    int pad[3];
 };
 static_assert(sizeof(DevCounters) == 64, "DevCounters layout");
 
@@ -37,7 +39,6 @@ struct CountCfg {
     int warp_max_out_degree;   // T_w
     int warp_area_ints;        // per-warp table area
     int warp_min_buckets;      // power of two
-    int max_levels;            // L cap of block tables
     int warps_per_block;       // warp kernel
     int warp_grid;             // persistent grid of the warp kernel
     int block_threads;         // block kernel
@@ -47,6 +48,7 @@ struct CountCfg {
     int chunk;
     int shard_count, shard_index;
     int record_timing;
+    int hash_mode;  // 0 multiplicative, 1 x mod B
 };
 
 // One graph of an orientation pass. A batch places its graphs in one padded
@@ -59,18 +61,23 @@ struct GraphRef {
 };
 
 // ---- orientation (orient.cu) ----------------------------------------------
+// Rows longer than this are oriented by one thread block each instead of
+// inside a 32-row warp group.
+constexpr int HUB_DEGREE = 1024;
 // deg, kept: int32[n]; partial: int64[scan_blocks(n)+1]; dag_ptr: int32[n+1];
 // warp_list: int32[n]; warp_desc: int2[n]; items: int2[item_cap].
 int scan_blocks(int64_t n);
+// hubs: int32[n] list of rows with degree > HUB_DEGREE (scratch).
 cudaError_t launch_orient(const void* row_ptr, int offset_bits, const int32_t* col, int64_t n, int64_t nnz,
                           int32_t* deg, int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
-                          int64_t dag_cap, DevCounters* ctr, int num_sms, cudaStream_t st, long long* launches);
+                          int64_t dag_cap, int32_t* hubs, DevCounters* ctr, int num_sms, cudaStream_t st,
+                          long long* launches);
 
 // Orientation of k graphs at once (device array of GraphRef, bases ascending)
 // into one DAG over the padded global vertex space [0, total).
 cudaError_t launch_orient_batch(const GraphRef* graphs, int k, int offset_bits, int64_t total, int32_t* deg,
                                 int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
-                                int64_t dag_cap, DevCounters* ctr, int num_sms, cudaStream_t st,
+                                int64_t dag_cap, int32_t* hubs, DevCounters* ctr, int num_sms, cudaStream_t st,
                                 long long* launches);
 
 // Binning (Sec. 4.3) from an existing DAG: fills warp_list / items / counters.
@@ -83,6 +90,7 @@ cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t
                          const int2* warp_desc, const int2* items, unsigned long long* per_vertex,
                          const CountCfg& cfg, DevCounters* ctr, cudaStream_t st, long long* launches);
 int count_block_budget_ints(const CountCfg& cfg);
+int count_block_part_max(const CountCfg& cfg);
 // ints of one warp-worker table for out-degree d (2*nextpow2(d) buckets of 4 slots + byte lengths)
 int pack_table_ints(int max_out_degree, int min_buckets);
 cudaError_t count_kernel_setup(CountCfg& cfg, int num_sms);

@@ -158,15 +158,17 @@ def test_per_vertex_counts(ctx):
 # ------------------------------------------------------ worker/table regimes
 
 PARAM_SETS = {
-    "tiny_levels": dict(max_levels=2),                         # block-table overflow chains everywhere
+    "tiny_block_items": dict(warp_max_out_degree=8, item_neighbors=32),  # many block items per vertex
     "one_table_per_pack": dict(warp_max_out_degree=12, warp_area_ints=136),
     "all_block": dict(warp_max_out_degree=1),                  # every vertex on the block path
     "all_warp": dict(warp_max_out_degree=255, warp_area_ints=2176, warps_per_block=4),
     "one_per_pop": dict(chunk=1),
     "big_min_buckets": dict(warp_min_buckets=512, warp_area_ints=2176),
     "small_items": dict(item_neighbors=32, warp_max_out_degree=16),
-    "split_parts": dict(block_threads=64, block_smem_bytes=4096, warp_max_out_degree=8),  # part_max = 256
+    "split_parts": dict(block_threads=64, block_smem_bytes=8192, item_neighbors=64, warp_max_out_degree=8),
+    # ^ part_max = 256: out-lists longer than 256 are probed part by part
     "chunk7": dict(chunk=7, warp_area_ints=4608),
+    "paper_hash": dict(hash_mode=1),
 }
 
 
@@ -188,13 +190,16 @@ def _bucket_collision_graph(k, stride=1024):
 
 
 @pytest.mark.parametrize("k,params", [(60, {}), (300, {}), (200, dict(warp_max_out_degree=255, warp_area_ints=2176)),
-                                      (300, dict(max_levels=2)), (500, dict(block_threads=64,
-                                                                            block_smem_bytes=4096))])
-def test_adversarial_overflow(T, k, params):
+                                      (600, {}), (500, dict(block_threads=64, block_smem_bytes=8192,
+                                                             item_neighbors=64))])
+@pytest.mark.parametrize("hash_mode", [1, 0])
+def test_adversarial_overflow(T, k, params, hash_mode):
+    # with Algorithm 1's hash (x mod B, hash_mode 1) every key of N+(0) lands in
+    # bucket 0 and the overflow chains run through hundreds of buckets
     g = _bucket_collision_graph(k)
     want = math.comb(k, 2) + math.comb(k, 3)
     assert oracle.count(g) == want
-    with T.Context(0, params=params) as c:
+    with T.Context(0, params=dict(params, hash_mode=hash_mode)) as c:
         assert gpu_count(c, g) == want
 
 
@@ -275,9 +280,9 @@ def test_asymmetric_input_does_not_overflow(T, ctx):
 
 
 def test_invalid_params(T):
-    for bad in (dict(warp_min_buckets=48), dict(max_levels=1), dict(shard_count=2, shard_index=2),
+    for bad in (dict(warp_min_buckets=48), dict(item_neighbors=2048), dict(shard_count=2, shard_index=2),
                 dict(warp_max_out_degree=256), dict(block_threads=100), dict(chunk=33), dict(warp_area_ints=320),
-                dict(warp_min_buckets=8)):
+                dict(warp_min_buckets=8), dict(hash_mode=2)):
         with pytest.raises(T.TcError) as ei:
             T.Context(0, params=bad)
         assert ei.value.status == T.TC_ERR_INVALID_ARG
@@ -289,7 +294,7 @@ def test_phase_timing_and_launch_count(T):
         rp, col = dev(g)
         l0 = c.kernel_launches()
         assert c.count(g.n, rp, col) == oracle.count(g)
-        assert c.kernel_launches() - l0 == 10   # 6 orientation + bin + 2 counting + finish
+        assert c.kernel_launches() - l0 == 12   # 8 orientation + bin + 2 counting + finish
         t = c.read_timing()
         assert t["calls"] == 1 and t["orient_ms"] > 0 and t["count_ms"] > 0
         assert c.read_timing()["calls"] == 0
