@@ -147,6 +147,110 @@ def count_phase_bytes(n: int, m: int, wplus: int) -> int:
     return 4 * (n + 1) + 4 * m + 8 * m + 4 * wplus
 
 
+# ------------------------------------------------- batched and served graphs
+
+BATCH = dict(name="batch-4096-seed4", graphs=4096, seed=4)
+SERVE = dict(rate=2000.0, pool=256, pool_seed=5, big_fraction=0.01, big_scale=22, budget_gb=40, seed=5)
+
+
+def measure_batched(T, torch, dev, steps: int):
+    """tc_count_batch over the 4096-graph batch (CUDA-graph replay) against a
+    loop of tc_count over the same graphs, on the same GPU."""
+    import numpy as np
+
+    import graphgen as G
+    t0 = time.time()
+    gs = G.batch(BATCH["seed"], BATCH["graphs"])
+    gen_s = time.time() - t0
+    tensors = [(g.n, torch.from_numpy(g.row_ptr.astype(np.int32)).to(dev),
+                torch.from_numpy(np.ascontiguousarray(g.col, dtype=np.int32)).to(dev)) for g in gs]
+    edges = sum(g.m for g in gs)
+    with T.Context(dev.index) as c:
+        counts = c.count_batch(tensors)  # first call captures the CUDA graph
+        c.count_batch(tensors)
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        for _ in range(steps):
+            c.count_batch(tensors)
+        batch_s = (time.perf_counter() - t) / steps
+        loop = [c.count(n, rp, col) for n, rp, col in tensors[:64]]  # warm-up
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        loop = [c.count(n, rp, col) for n, rp, col in tensors]
+        loop_s = time.perf_counter() - t
+    import oracle
+    sample = list(range(0, BATCH["graphs"], BATCH["graphs"] // 32))
+    want = [oracle.count(gs[i]) for i in sample]
+    return {
+        "workload": BATCH["name"], "graphs": len(gs), "edges": edges, "generation_s": round(gen_s, 1),
+        "ms_per_batch": batch_s * 1e3, "graphs_per_s": len(gs) / batch_s, "edges_per_s": edges / batch_s,
+        "loop_graphs_per_s": len(gs) / loop_s, "speedup_vs_loop": loop_s / batch_s, "steps": steps,
+        "parity": {"batch_equals_loop": counts == loop,
+                   "oracle_sample": len(sample), "oracle_equal": [counts[i] for i in sample] == want},
+    }
+
+
+def measure_serving(T, torch, dev, seconds: float):
+    """Poisson arrivals (rate 2000/s) of requests drawn from the batched
+    distribution, 1% R-MAT scale-22 graphs, admitted under a 40 GB budget;
+    submit -> poll-ready latency and completed graphs/s."""
+    import numpy as np
+
+    import graphgen as G
+    pool = G.batch(SERVE["pool_seed"], SERVE["pool"])
+    big = [G.rmat(SERVE["big_scale"], 16, seed=SERVE["seed"] + i) for i in range(2)]
+    graphs = pool + big
+    pinned = []
+    for g in graphs:
+        rp = torch.from_numpy(g.row_ptr.astype(np.int32)).pin_memory()
+        col = torch.from_numpy(np.ascontiguousarray(g.col, dtype=np.int32)).pin_memory()
+        pinned.append((g.n, rp, col, rp.numpy(), col.numpy()))
+    with T.Context(dev.index) as c:  # every graph counted alone first
+        alone = [c.count(n, rp.to(dev), col.to(dev)) for n, rp, col, _, _ in pinned]
+    rng = np.random.default_rng(SERVE["seed"])
+    n_req = max(1, int(SERVE["rate"] * seconds))
+    arrivals = np.cumsum(rng.exponential(1.0 / SERVE["rate"], n_req))
+    pick = np.where(rng.random(n_req) < SERVE["big_fraction"], len(pool) + rng.integers(0, len(big), n_req),
+                    rng.integers(0, len(pool), n_req))
+    with T.Context(dev.index, mem_budget=SERVE["budget_gb"] << 30) as c:
+        warm = c.submit_borrowed(pinned[0][0], pinned[0][3], pinned[0][4])  # starts the serving worker
+        c.drain()
+        assert c.poll(warm) == alone[0]
+        submit_t = np.zeros(n_req)
+        done_t = np.zeros(n_req)
+        result = [None] * n_req
+        outstanding = {}
+        nxt = 0
+        t0 = time.perf_counter()
+        while nxt < n_req or outstanding:
+            now = time.perf_counter() - t0
+            while nxt < n_req and arrivals[nxt] <= now:
+                n, _, _, rp_np, col_np = pinned[pick[nxt]]
+                outstanding[c.submit_borrowed(n, rp_np, col_np)] = nxt
+                submit_t[nxt] = time.perf_counter() - t0
+                nxt += 1
+            for tk in list(outstanding):
+                v = c.poll(tk)
+                if v is not None:
+                    i = outstanding.pop(tk)
+                    done_t[i] = time.perf_counter() - t0
+                    result[i] = v
+            if nxt < n_req and not outstanding:
+                time.sleep(max(0.0, min(arrivals[nxt] - (time.perf_counter() - t0), 0.001)))
+    lat = (done_t - submit_t) * 1e3
+    edges = sum(graphs[i].m for i in pick)
+    span = done_t.max() - submit_t.min()
+    return {
+        "arrival_rate_per_s": SERVE["rate"], "seconds": seconds, "requests": n_req,
+        "big_requests": int((pick >= len(pool)).sum()), "budget_gb": SERVE["budget_gb"],
+        "graphs_per_s": n_req / span, "edges_per_s": edges / span,
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+        "identical_to_alone": all(result[i] == alone[pick[i]] for i in range(n_req)),
+        "submission": "tc_submit_borrowed from pinned host memory",
+    }
+
+
 # -------------------------------------------------------------- the arms
 
 def run_gb300(args):
@@ -285,6 +389,10 @@ def run_gb300(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if args.batched:
+        result["batched"] = measure_batched(T, torch, dev, steps=args.batch_steps)
+    if args.serve_seconds > 0:
+        result["serving"] = measure_serving(T, torch, dev, args.serve_seconds)
     if not args.no_cpu_baseline:
         import oracle
         cores = oracle.max_threads()
@@ -335,6 +443,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", type=int, default=1, help="1: also time the 4096-graph batch (rank 0)")
+    ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="seconds of Poisson arrivals for the serving measurement (0: skip; the config is 60)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

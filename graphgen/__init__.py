@@ -77,6 +77,8 @@ def _lib():
             lib.gg_batch_spec.restype = None
             lib.gg_batch_spec.argtypes = [ctypes.c_uint64, ctypes.c_int64, I32P, I64P, F64P]
             lib.gg_num_threads.restype = ctypes.c_int
+            lib.gg_set_threads.restype = None
+            lib.gg_set_threads.argtypes = [ctypes.c_int]
             _lib_handle = lib
     return _lib_handle
 
@@ -220,8 +222,21 @@ def batch_graph(seed: int, idx: int) -> Csr:
     return g
 
 
-def batch(seed: int, k: int) -> list:
-    return [batch_graph(seed, i) for i in range(k)]
+def batch(seed: int, k: int, threads: int = 0) -> list:
+    """Graphs 0..k-1 of the batched workload, generated by `threads` host
+    threads (default: all cores), each running its C calls single-threaded."""
+    import concurrent.futures as cf
+    threads = threads or os.cpu_count() or 1
+    if threads == 1:
+        return [batch_graph(seed, i) for i in range(k)]
+    lib = _lib()
+
+    def one(i):
+        lib.gg_set_threads(1)
+        return batch_graph(seed, i)
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        return list(ex.map(one, range(k)))
 
 
 # --------------------------------------------- small closed-form families

@@ -330,6 +330,15 @@ void gg_batch_spec(uint64_t seed, int64_t idx, int32_t* kind, int64_t* n, double
     *mean_deg = 4.0 + 60.0 * u01(gg_draw(key, 2));
 }
 
+/* OpenMP threads for parallel regions started by the calling thread. */
+void gg_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int gg_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

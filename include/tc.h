@@ -30,8 +30,8 @@
  *     stream). Device inputs must stay valid and unmodified until the call
  *     returns (blocking calls) or until the stream reaches the call's work
  *     (the *_async calls).
- *   - A context is not thread-safe, except tc_submit / tc_poll / tc_drain,
- *     which may be called from any thread at any time.
+ *   - A context is not thread-safe, except tc_submit / tc_submit_borrowed /
+ *     tc_poll / tc_drain, which may be called from any thread at any time.
  *
  * Input preconditions (not all checked): the CSR is symmetric (v in N(u) iff
  * u in N(v)) with no duplicate entries in a row; rows need not be sorted;
@@ -228,6 +228,14 @@ tc_status tc_count_batch(tc_ctx* ctx, const tc_csr* gs, int32_t k, uint64_t* cou
  * the GPU (continuous batching). *ticket identifies the request.
  * TC_ERR_BUSY: the request alone exceeds the budget. */
 tc_status tc_submit(tc_ctx* ctx, const tc_csr* g, uint64_t* ticket);
+
+/* Like tc_submit, without the host copy and without the host-side input
+ * check: the library reads the caller's host arrays g->row_ptr / g->col when
+ * the request is admitted (pinned memory lets that copy run as DMA). The
+ * caller keeps them alive and unchanged until tc_poll has reported the
+ * request finished. A malformed graph is still detected, on the device, but
+ * then fails every request of the round it ran in. */
+tc_status tc_submit_borrowed(tc_ctx* ctx, const tc_csr* g, uint64_t* ticket);
 
 /* TC_OK and *count once request `ticket` finished (the ticket is then
  * retired); TC_ERR_NOT_READY while it is queued or running; the request's own

@@ -221,6 +221,14 @@ class Context:
         self._check(_tc.tc_submit(self.handle, ctypes.byref(g), ctypes.byref(t)))
         return int(t.value)
 
+    def submit_borrowed(self, n: int, row_ptr, col) -> int:
+        """Zero-copy submission: row_ptr / col (host arrays, ideally pinned) must
+        stay alive and unchanged until poll() returns the count."""
+        g = make_csr(n, row_ptr, col)
+        t = ctypes.c_uint64()
+        self._check(_tc.tc_submit_borrowed(self.handle, ctypes.byref(g), ctypes.byref(t)))
+        return int(t.value)
+
     def poll(self, ticket: int):
         """The count, or None while the request is not finished."""
         out = ctypes.c_uint64()

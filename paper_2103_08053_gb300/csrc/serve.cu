@@ -40,8 +40,10 @@ struct Request {
     uint64_t ticket = 0;
     int64_t n = 0, nnz = 0;
     int bits = 32;
-    std::vector<unsigned char> h_rp;
+    std::vector<unsigned char> h_rp;  // library copies (tc_submit)
     std::vector<int32_t> h_col;
+    const void* src_rp = nullptr;     // the caller's arrays (tc_submit_borrowed)
+    const int32_t* src_col = nullptr;
     size_t off = 0, bytes = 0;  // arena placement
     ReqState state = ReqState::Queued;
     tc_status status = TC_OK;
@@ -149,9 +151,10 @@ tc_status start_round(tc_ctx* ctx, ServeState& S, Round& r) {
         unsigned char* base = S.arena_base + q->off;
         const size_t rp_bytes = (size_t)(q->n + 1) * (q->bits / 8);
         unsigned char* d_col = base + (rp_bytes + kAlign - 1) / kAlign * kAlign;
-        cudaError_t e = cudaMemcpyAsync(base, q->h_rp.data(), rp_bytes, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess && q->nnz)
-            e = cudaMemcpyAsync(d_col, q->h_col.data(), (size_t)q->nnz * 4, cudaMemcpyHostToDevice, st);
+        const void* hrp = q->src_rp ? q->src_rp : q->h_rp.data();
+        const void* hcol = q->src_col ? (const void*)q->src_col : (const void*)q->h_col.data();
+        cudaError_t e = cudaMemcpyAsync(base, hrp, rp_bytes, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && q->nnz) e = cudaMemcpyAsync(d_col, hcol, (size_t)q->nnz * 4, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_status(ctx, e, "serving: copying a request to the device");
         gs[i] = tc_csr{q->n, q->nnz, base, q->bits, reinterpret_cast<const int32_t*>(d_col)};
     }
@@ -305,7 +308,11 @@ void serve_shutdown(tc_ctx* ctx) {
 
 extern "C" {
 
-tc_status tc_submit(tc_ctx* ctx, const tc_csr* g, uint64_t* ticket) {
+}  // extern "C"
+
+namespace {
+
+tc_status submit_common(tc_ctx* ctx, const tc_csr* g, bool borrowed, uint64_t* ticket) {
     if (!ctx || !ticket) return TC_ERR_INVALID_ARG;
     tc_status s = check_csr(ctx, g);
     if (s) return s;
@@ -326,17 +333,20 @@ tc_status tc_submit(tc_ctx* ctx, const tc_csr* g, uint64_t* ticket) {
     q->nnz = g->nnz;
     q->bits = g->offset_bits;
     q->bytes = bytes;
-    try {
-        q->h_rp.resize((size_t)(g->n + 1) * (g->offset_bits / 8));
-        q->h_col.resize((size_t)g->nnz);
-    } catch (...) {
-        delete q;
-        return ctx_fail(ctx, TC_ERR_OOM, "host memory for the request copy");
-    }
-    if (g->n >= 0 && g->row_ptr) memcpy(q->h_rp.data(), g->row_ptr, q->h_rp.size());
-    if (g->nnz) memcpy(q->h_col.data(), g->col, (size_t)g->nnz * 4);
-    // a malformed request is refused here, so it cannot fail the round it would join
-    {
+    if (borrowed) {
+        q->src_rp = g->row_ptr;
+        q->src_col = g->col;
+    } else {
+        try {
+            q->h_rp.resize((size_t)(g->n + 1) * (g->offset_bits / 8));
+            q->h_col.resize((size_t)g->nnz);
+        } catch (...) {
+            delete q;
+            return ctx_fail(ctx, TC_ERR_OOM, "host memory for the request copy");
+        }
+        if (g->row_ptr) memcpy(q->h_rp.data(), g->row_ptr, q->h_rp.size());
+        if (g->nnz) memcpy(q->h_col.data(), g->col, (size_t)g->nnz * 4);
+        // a malformed request is refused here, so it cannot fail the round it would join
         long long prev = 0;
         bool bad = false;
         for (int64_t u = 0; u <= g->n && !bad; ++u) {
@@ -362,6 +372,16 @@ tc_status tc_submit(tc_ctx* ctx, const tc_csr* g, uint64_t* ticket) {
     }
     S.cv_work.notify_one();
     return TC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tc_status tc_submit(tc_ctx* ctx, const tc_csr* g, uint64_t* ticket) { return submit_common(ctx, g, false, ticket); }
+
+tc_status tc_submit_borrowed(tc_ctx* ctx, const tc_csr* g, uint64_t* ticket) {
+    return submit_common(ctx, g, true, ticket);
 }
 
 tc_status tc_poll(tc_ctx* ctx, uint64_t ticket, uint64_t* count) {

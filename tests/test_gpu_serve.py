@@ -111,3 +111,12 @@ def test_serve_errors(T):
         with pytest.raises(T.TcError) as ei:
             c.submit(*host(G.complete(4)))
         assert ei.value.status == T.TC_ERR_INVALID_ARG
+
+
+def test_borrowed_submission(T):
+    gs = [G.batch_graph(21, i) for i in range(30)] + [G.complete(150)]
+    want = [oracle.count(g) for g in gs]
+    keep = [host(g, 64 if i % 3 == 0 else 32) for i, g in enumerate(gs)]  # caller keeps these alive
+    with T.Context(0, mem_budget=1 << 30) as c:
+        tickets = [c.submit_borrowed(*h) for h in keep]
+        assert wait_all(c, tickets) == want
