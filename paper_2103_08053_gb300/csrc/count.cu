@@ -172,6 +172,30 @@ __device__ __noinline__ int probe_b4_chain(const int* sm, int tab, int mask, int
     return 0;
 }
 
+// VC_UNROLL probes per lane: key[q] against the table at int offset kt[q]
+// with log2 B = km[q] & 0xffff (pack slot km[q] >> 16). A probe is one
+// 16-byte load and four compares; only a lane whose bucket is full and did
+// not match walks the overflow chain. NOKEY lanes never match.
+template <bool SLOT_HITS, int HM>
+__device__ __forceinline__ uint32_t probe4(const int (&key)[VC_UNROLL], const int (&kt)[VC_UNROLL],
+                                           const int (&km)[VC_UNROLL], const int* sm, int* stage) {
+    uint32_t hits = 0;
+#pragma unroll
+    for (int q = 0; q < VC_UNROLL; ++q) {
+        const int lg = km[q] & 0xffff;
+        const int h = bucket_of<HM>(key[q], lg);
+        const int4 b4 = *reinterpret_cast<const int4*>(sm + kt[q] + 4 * h);
+        int hit = match4(b4, key[q]);
+        const bool more = key[q] >= 0 && !hit && b4.w != EMPTY;
+        if (__any_sync(FULL, more)) {
+            if (more) hit = probe_b4_chain(sm, kt[q], (1 << lg) - 1, h, key[q]);
+        }
+        hits += hit;
+        if (SLOT_HITS && hit) atomicAdd(&stage[128 + (km[q] >> 16)], 1);
+    }
+    return hits;
+}
+
 // Probe the 2-hop lists of up to 32 out-edges against bucket-of-4 tables.
 // Lane i brings the list N+(v_i) = dag_col[s, s+l) and the table of its edge
 // (tab: int offset of the slots, lgB = log2 B, slot: pack slot). Empty lists
@@ -224,24 +248,13 @@ __device__ __forceinline__ uint32_t vc_range_b4(int s, int l, int tab, int lgB, 
             const int f = b + lane;
             key[q] = (f < end) ? __ldg(dag_col + bo + f) : NOKEY;
         }
-#pragma unroll
-        for (int q = 0; q < VC_UNROLL; ++q) {
-            const int lg = km[q] & 0xffff;
-            const int h = bucket_of<HM>(key[q], lg);
-            const int4 b4 = *reinterpret_cast<const int4*>(sm + kt[q] + 4 * h);
-            int hit = match4(b4, key[q]);
-            const bool more = key[q] >= 0 && !hit && b4.w != EMPTY;
-            if (__any_sync(FULL, more)) {
-                if (more) hit = probe_b4_chain(sm, kt[q], (1 << lg) - 1, h, key[q]);
-            }
-            hits += hit;
-            if (SLOT_HITS && hit) atomicAdd(&stage[128 + (km[q] >> 16)], 1);
-        }
+        hits += probe4<SLOT_HITS, HM>(key, kt, km, sm, stage);
     }
     *done = end > skip ? end - skip : 0;
     return hits;
 }
 
+// Whole 2-hop lists of up to 32 out-edges (warp workers).
 template <bool SLOT_HITS, int HM>
 __device__ __forceinline__ uint32_t vc_probe_b4(int s, int l, int tab, int lgB, int slot, const int* sm,
                                                 const int32_t* __restrict__ dag_col, int lane, int* stage) {

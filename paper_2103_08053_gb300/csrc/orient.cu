@@ -124,6 +124,9 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
         st[lane] = vin - len;
         as[lane] = a;
         if (lane == 31) st[32] = vin;
+        // without hub rows the walk is the plain concatenation starting at gb0
+        const bool hubless = __shfl_sync(FULL, vin, 31) == e - __shfl_sync(FULL, a, 0);
+        const long long gb0 = __shfl_sync(FULL, a, 0);
         cnt[lane] = 0;
         if (COMPACT) dp[lane] = (lane < nr) ? dag_ptr[g * 32 + lane] : 0;
         __syncwarp();
@@ -136,10 +139,13 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
 #pragma unroll
             for (int q = 0; q < ORIENT_UNROLL; ++q) {
                 const long long f = base + 32 * q + lane;
-                int rq = r;
-                if (f < ge)
+                long long at = gb0 + f;
+                if (!hubless && f < ge) {
+                    int rq = r;
                     while (st[rq + 1] <= f) ++rq;
-                vq[q] = (f < ge) ? __ldg(col + as[rq] + (f - st[rq])) : -1;
+                    at = as[rq] + (f - st[rq]);
+                }
+                vq[q] = (f < ge) ? __ldg(col + at) : -1;
             }
 #pragma unroll
             for (int q = 0; q < ORIENT_UNROLL; ++q)
@@ -155,7 +161,7 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
                     if ((unsigned)v >= (unsigned long long)n) {
                         atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
                     } else {
-                        const int du = deg[vb + u0 + r];
+                        const int du = (int)(st[r + 1] - st[r]);  // rows in the walk are not hubs
                         const int dv = dq[q];
                         keep = (dv > du) || (dv == du && (int64_t)v > u0 + r);
                     }
