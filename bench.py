@@ -166,6 +166,10 @@ def measure_batched(T, torch, dev, steps: int):
                 torch.from_numpy(np.ascontiguousarray(g.col, dtype=np.int32)).to(dev)) for g in gs]
     edges = sum(g.m for g in gs)
     with T.Context(dev.index) as c:
+        t = time.time()
+        tuned = c.autotune(tensors, cache_path=os.path.join(ROOT, "gpurun_out", "tune_cache.txt")
+                           if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+        tune_s = time.time() - t
         counts = c.count_batch(tensors)  # first call captures the CUDA graph
         c.count_batch(tensors)
         torch.cuda.synchronize(dev)
@@ -185,6 +189,8 @@ def measure_batched(T, torch, dev, steps: int):
         "workload": BATCH["name"], "graphs": len(gs), "edges": edges, "generation_s": round(gen_s, 1),
         "ms_per_batch": batch_s * 1e3, "graphs_per_s": len(gs) / batch_s, "edges_per_s": edges / batch_s,
         "loop_graphs_per_s": len(gs) / loop_s, "speedup_vs_loop": loop_s / batch_s, "steps": steps,
+        "autotuned": {k: tuned[k] for k in ("warp_max_out_degree", "warp_area_ints", "warp_min_buckets", "chunk",
+                                             "warps_per_block", "item_neighbors")}, "tune_s": round(tune_s, 1),
         "parity": {"batch_equals_loop": counts == loop,
                    "oracle_sample": len(sample), "oracle_equal": [counts[i] for i in sample] == want},
     }

@@ -219,6 +219,17 @@ tc_status tc_count_dag_noalloc(const tc_dag* dag, uint64_t* count_device, int32_
  * counts_host: k results. Blocks. */
 tc_status tc_count_batch(tc_ctx* ctx, const tc_csr* gs, int32_t k, uint64_t* counts_host, void* stream);
 
+/* Autotuner: time the workload gs[0..k) (tc_count for k == 1, tc_count_batch
+ * otherwise) under candidate values of warp_max_out_degree (with the table
+ * area it needs), warp_min_buckets, chunk, warps_per_block and
+ * item_neighbors, one knob at a time, keep the fastest on ctx and return them
+ * in *best (may be NULL). gs: device CSRs. cache_path: NULL, or a text file
+ * where results are appended per workload signature (graph count, vertex and
+ * entry totals in powers of two, offset width) and looked up first. The counts
+ * of every trial must agree; a trial that disagrees is rejected. Blocks. */
+tc_status tc_autotune(tc_ctx* ctx, const tc_csr* gs, int32_t k, const char* cache_path, tc_params* best,
+                      void* stream);
+
 /* ---- serving -------------------------------------------------------------- */
 
 /* Queue a counting request. g: HOST CSR; the library copies it into its own

@@ -214,6 +214,18 @@ class Context:
         self._check(_tc.tc_count_batch(self.handle, arr, k, out, _stream_handle(stream)))
         return [int(out[i]) for i in range(k)]
 
+    def autotune(self, graphs, cache_path: str | None = None, stream=None) -> dict:
+        """Tune the worker/table parameters on `graphs` ((n, row_ptr, col)
+        device arrays); keeps the best on this context and returns them."""
+        k = len(graphs)
+        arr = (tc_csr * max(k, 1))()
+        for i, (n, rp, col) in enumerate(graphs):
+            arr[i] = make_csr(n, rp, col)
+        p = tc_params()
+        self._check(_tc.tc_autotune(self.handle, arr, k, cache_path.encode() if cache_path else None,
+                                    ctypes.byref(p), _stream_handle(stream)))
+        return {f: getattr(p, f) for f, _ in tc_params._fields_ if f != "reserved"}
+
     # serving
     def submit(self, n: int, row_ptr: np.ndarray, col: np.ndarray) -> int:
         g = make_csr(n, row_ptr, col)

@@ -81,6 +81,7 @@ _protos = {
     "tc_count_host": (c_int32, [c_void_p, _P(tc_csr), _P(c_uint64), c_void_p]),
     "tc_dag_stats": (c_int32, [c_void_p, _P(tc_dag), _P(tc_stats), c_void_p]),
     "tc_count_batch": (c_int32, [c_void_p, _P(tc_csr), c_int32, _P(c_uint64), c_void_p]),
+    "tc_autotune": (c_int32, [c_void_p, _P(tc_csr), c_int32, ctypes.c_char_p, _P(tc_params), c_void_p]),
     "tc_submit": (c_int32, [c_void_p, _P(tc_csr), _P(c_uint64)]),
     "tc_submit_borrowed": (c_int32, [c_void_p, _P(tc_csr), _P(c_uint64)]),
     "tc_poll": (c_int32, [c_void_p, c_uint64, _P(c_uint64)]),

@@ -85,3 +85,25 @@ def test_batched_workload_sample(T):
     want = [oracle.count(g) for g in gs]
     with T.Context(0) as c:
         assert c.count_batch([dev(g) for g in gs]) == want
+
+
+def test_autotune_keeps_counts_and_caches(T, tmp_path):
+    gs = [G.batch_graph(31, i) for i in range(48)]
+    want = [oracle.count(g) for g in gs]
+    cache = str(tmp_path / "tune.txt")
+    with T.Context(0) as c:
+        tensors = [dev(g) for g in gs]
+        best = c.autotune(tensors, cache_path=cache)
+        assert c.get_params()["warp_max_out_degree"] == best["warp_max_out_degree"]
+        assert c.count_batch(tensors) == want
+    lines = open(cache).read().splitlines()
+    assert len(lines) == 1 and lines[0].startswith("sig ")
+    with T.Context(0) as c:            # the second tuner reads the cache
+        again = c.autotune([dev(g) for g in gs], cache_path=cache)
+        assert again == best
+        assert c.count_batch([dev(g) for g in gs]) == want
+    assert len(open(cache).read().splitlines()) == 1
+    with T.Context(0) as c:            # one graph: tuned with tc_count
+        g = G.rmat(14, 16, seed=32)
+        c.autotune([dev(g)])
+        assert c.count(*dev(g)) == oracle.count(g)

@@ -1,0 +1,100 @@
+"""Parity at the workloads' full sizes, in the launch configuration bench.py
+uses (default parameters, one context).
+
+* the bench workload (RGG, 2^22 points, mean degree 64): whole count vs oracle;
+* R-MAT scale 16: whole count vs oracle;
+* R-MAT scale 26 with int64 offsets: per-vertex counts of a sample of vertices
+  vs the oracle's, and the per-vertex sum equal to the total;
+* the 4096-graph batched workload: batch vs per-graph loop vs oracle sample;
+* the dataset table's 3Dgrid row (a 464^3 periodic grid): |V|, |E| and the
+  count (0) exactly as printed.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import graphgen as G
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def T():
+    import __graft_entry__ as ge
+    ge._load_builder().build()
+    import paper_2103_08053_gb300 as T
+    return T
+
+
+def dev(g, bits=32):
+    d = torch.device("cuda", 0)
+    rp = torch.from_numpy(g.row_ptr.astype(np.int64 if bits == 64 else np.int32)).to(d)
+    col = torch.from_numpy(np.ascontiguousarray(g.col, dtype=np.int32)).to(d)
+    return g.n, rp, col
+
+
+def test_bench_workload_whole_count(T):
+    g = G.workload("rgg22")
+    want = oracle.count(g)
+    with T.Context(0) as c:
+        n, rp, col = dev(g)
+        assert c.count(n, rp, col) == want
+        out = torch.zeros(1, dtype=torch.int64, device="cuda")
+        err = torch.zeros(1, dtype=torch.int32, device="cuda")
+        c.count_async(n, rp, col, out, err)
+        torch.cuda.synchronize()
+        assert int(out.item()) == want and int(err.item()) == 0
+
+
+def test_rmat16_whole_count(T):
+    g = G.workload("rmat16")
+    with T.Context(0) as c:
+        assert c.count(*dev(g)) == oracle.count(g)
+
+
+def test_rmat26_sampled_per_vertex(T):
+    g = G.workload("rmat26")
+    assert g.nnz > 1_000_000_000
+    with T.Context(0) as c:
+        n, rp, col = dev(g, 64)
+        total = c.count(n, rp, col)
+        d = c.orient(n, rp, col)
+        pv = torch.zeros(n, dtype=torch.int64, device="cuda")
+        assert c.count_dag(d, per_vertex=pv) == total
+        assert int(pv.sum().item()) == total
+        od = oracle.orient(g)
+        assert d.m == od.m == g.m
+        dp, _ = d.tensors()
+        assert np.array_equal(dp.cpu().numpy().astype(np.int64), od.dag_ptr)
+        deg = od.out_degrees()
+        rng = np.random.default_rng(26)
+        # every vertex with the largest out-degrees, plus a random sample
+        us = np.unique(np.concatenate([np.argsort(deg)[-200:], rng.integers(0, n, 2000)]))
+        want = oracle.count_dag_at(od, us)
+        got = pv[torch.from_numpy(us).cuda()].cpu().numpy().astype(np.uint64)
+        assert np.array_equal(got, want)
+        d.free()
+
+
+def test_batched_workload_4096(T):
+    gs = G.batch(4, 4096)
+    with T.Context(0) as c:
+        tensors = [dev(g) for g in gs]
+        counts = c.count_batch(tensors)
+        assert counts == [c.count(*t) for t in tensors]
+    for i in range(0, 4096, 128):
+        assert counts[i] == oracle.count(gs[i])
+
+
+def test_3dgrid_dataset_row(T):
+    row = json.load(open(os.path.join(GOLDEN, "dataset_3dgrid.json")))
+    g = G.torus3d(464)
+    assert g.n == row["V"] and g.m == row["E"]
+    with T.Context(0) as c:
+        assert c.count(*dev(g)) == row["triangles"] == oracle.count(g)
