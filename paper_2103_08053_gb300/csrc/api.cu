@@ -153,12 +153,12 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "need 0 <= shard_index < shard_count");
     const int max_smem = ctx ? ctx->max_smem_optin : 227 * 1024;
     const long long warp_smem =
-        (long long)p.warps_per_block * (p.warp_area_ints + 160) * 4;
+        (long long)p.warps_per_block * (p.warp_area_ints + 224) * 4;
     if (warp_smem > max_smem)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "warp kernel needs %lld B of shared memory (max %d)", warp_smem,
                         max_smem);
     if (p.block_smem_bytes > max_smem || p.block_smem_bytes % 16 ||
-        p.block_smem_bytes / 4 - (p.block_threads / 32) * 160 - 2 * p.item_neighbors < 5 * 64)
+        p.block_smem_bytes / 4 - (p.block_threads / 32) * 128 - 2 * p.item_neighbors < 5 * 64)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "block_smem_bytes out of range (max %d)", max_smem);
     if (out) *out = p;
     if (cfg) {

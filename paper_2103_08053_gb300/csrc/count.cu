@@ -62,7 +62,7 @@ namespace {
 #ifndef VC_UNROLL
 #define VC_UNROLL 4
 #endif
-static_assert(VC_UNROLL >= 1 && VC_UNROLL <= 4, "VC_UNROLL in [1, 4]");
+static_assert(VC_UNROLL == 4, "the bitmap owner path reads four window words at once");
 
 #ifndef PACK_MIN_BLOCKS
 #define PACK_MIN_BLOCKS 4
@@ -72,7 +72,8 @@ static_assert(VC_UNROLL >= 1 && VC_UNROLL <= 4, "VC_UNROLL in [1, 4]");
 #define BLOCK_PIECE 512  // combined 2-hop indices per piece of a thread-block item
 #endif
 
-constexpr int STAGE_INTS = 160;  // per warp: 4 x 32 compaction lanes | 32 slot hit counters
+constexpr int STAGE_INTS = 224;        // warp workers: 4 x 32 compaction lanes | 32 slot hits | 64-word bitmap
+constexpr int BLOCK_STAGE_INTS = 128;  // thread-block workers: 4 x 32 compaction lanes
 constexpr int EMPTY = -1;        // an unused slot (vertex ids are >= 0)
 constexpr int NOKEY = -2;        // the key of a lane with nothing to probe
 
@@ -113,11 +114,18 @@ __device__ __forceinline__ int vc_owner(int b, int P, int Pex, bool listlane, un
 // and probes walk long overflow chains -- the collisions the paper reduces by
 // reordering ids (Sec. 4.1). The multiplicative hash spreads any id set
 // evenly; the count does not depend on the hash.
-// HM = 1 selects Algorithm 1's own hash, x mod B.
+// HM = 1 selects Algorithm 1's own hash, x mod B. `mult` is the odd
+// multiplier of the multiplicative hash (a pack may switch to another one
+// to make its tables overflow-free, see k_count_pack).
+constexpr unsigned kHashMult0 = 0x9E3779B1u;  // 2^32 / golden ratio
+__device__ __forceinline__ unsigned hash_mult(int i) {
+    return i == 0 ? kHashMult0 : i == 1 ? 0x85EBCA77u : i == 2 ? 0xC2B2AE3Du : 0x27D4EB2Fu;
+}
+
 template <int HM>
-__device__ __forceinline__ int bucket_of(int w, int lgB) {
+__device__ __forceinline__ int bucket_of(int w, int lgB, unsigned mult = kHashMult0) {
     if (HM == 1) return w & ((1 << lgB) - 1);
-    return (int)(((unsigned)w * 0x9E3779B1u) >> (32 - lgB));
+    return (int)(((unsigned)w * mult) >> (32 - lgB));
 }
 
 // ---- pack tables (bucket-major, 4 slots, byte lengths) ---------------------
@@ -126,20 +134,22 @@ __device__ __forceinline__ int bucket_of(int w, int lgB) {
 // an atomic add on its length byte; a full bucket (4 claims) sends the key to
 // the next bucket. sm: shared array; tab/lenw: int offsets of the slots and
 // of the length words; B = 2^lgB. Lengths count claims (<= keys <= 255).
+// Returns 1 when the key did not fit its home bucket (the table overflowed).
 template <int HM>
-__device__ __forceinline__ void insert_b4(int* sm, int tab, int lenw, int lgB, int w) {
+__device__ __forceinline__ int insert_b4(int* sm, int tab, int lenw, int lgB, int w, unsigned mult) {
     const int mask = (1 << lgB) - 1;
-    int h = bucket_of<HM>(w, lgB);
+    int h = bucket_of<HM>(w, lgB, mult);
     for (int s = 0; s <= mask; ++s) {
         const int sh = 8 * (h & 3);
         const unsigned old = atomicAdd(reinterpret_cast<unsigned*>(sm + lenw + (h >> 2)), 1u << sh);
         const int slot = (old >> sh) & 0xff;
         if (slot < 4) {
             sm[tab + 4 * h + slot] = w;
-            return;
+            return s > 0;
         }
         h = (h + 1) & mask;
     }
+    return 1;
 }
 
 // Same claim with one 32-bit length word per bucket (thread-block tables,
@@ -178,12 +188,12 @@ __device__ __noinline__ int probe_b4_chain(const int* sm, int tab, int mask, int
 // not match walks the overflow chain. NOKEY lanes never match.
 template <bool SLOT_HITS, int HM>
 __device__ __forceinline__ uint32_t probe4(const int (&key)[VC_UNROLL], const int (&kt)[VC_UNROLL],
-                                           const int (&km)[VC_UNROLL], const int* sm, int* stage) {
+                                           const int (&km)[VC_UNROLL], const int* sm, int* stage, unsigned mult) {
     uint32_t hits = 0;
 #pragma unroll
     for (int q = 0; q < VC_UNROLL; ++q) {
         const int lg = km[q] & 0xffff;
-        const int h = bucket_of<HM>(key[q], lg);
+        const int h = bucket_of<HM>(key[q], lg, mult);
         const int4 b4 = *reinterpret_cast<const int4*>(sm + kt[q] + 4 * h);
         int hit = match4(b4, key[q]);
         const bool more = key[q] >= 0 && !hit && b4.w != EMPTY;
@@ -208,7 +218,7 @@ __device__ __forceinline__ uint32_t probe4(const int (&key)[VC_UNROLL], const in
 template <bool SLOT_HITS, int HM>
 __device__ __forceinline__ uint32_t vc_range_b4(int s, int l, int tab, int lgB, int slot, int skip, int limit,
                                                 const int* sm, const int32_t* __restrict__ dag_col, int lane,
-                                                int* stage, int* done) {
+                                                int* stage, int* done, unsigned mult = kHashMult0) {
     const unsigned nem = __ballot_sync(FULL, l > 0);
     if (nem == 0) {
         *done = 0;
@@ -248,18 +258,86 @@ __device__ __forceinline__ uint32_t vc_range_b4(int s, int l, int tab, int lgB, 
             const int f = b + lane;
             key[q] = (f < end) ? __ldg(dag_col + bo + f) : NOKEY;
         }
-        hits += probe4<SLOT_HITS, HM>(key, kt, km, sm, stage);
+        hits += probe4<SLOT_HITS, HM>(key, kt, km, sm, stage, mult);
     }
     *done = end > skip ? end - skip : 0;
     return hits;
 }
 
-// Whole 2-hop lists of up to 32 out-edges (warp workers).
+// Fast probe of whole 2-hop lists against overflow-free pack tables: every
+// key is in its home bucket, so one 16-byte load and four compares decide it.
+// Lane i brings N+(v_i) = dag_col[s, s+l) and its table descriptor
+// td = slots offset | log2 B << 16 | pack slot << 21. Owners of flat indices
+// come from a bitmap of list starts (bit f set iff a list starts at combined
+// index f) when the combined length fits BITMAP_BITS: owner of f = (number of
+// starts <= f) - 1, one shared load and two popcounts per window; longer
+// chunks use vc_owner.
+constexpr int BITMAP_WORDS = 64;  // 2048 combined indices
 template <bool SLOT_HITS, int HM>
-__device__ __forceinline__ uint32_t vc_probe_b4(int s, int l, int tab, int lgB, int slot, const int* sm,
-                                                const int32_t* __restrict__ dag_col, int lane, int* stage) {
-    int done;
-    return vc_range_b4<SLOT_HITS, HM>(s, l, tab, lgB, slot, 0, 0x7fffffff, sm, dag_col, lane, stage, &done);
+__device__ __forceinline__ uint32_t vc_pack_fast(int s, int l, int td, const int* sm,
+                                                 const int32_t* __restrict__ dag_col, int lane, int* stage,
+                                                 unsigned mult) {
+    const unsigned nem = __ballot_sync(FULL, l > 0);
+    if (nem == 0) return 0;
+    const int c = __popc(nem);
+    if (l > 0) {
+        const int p = __popc(nem & lanemask_lt(lane));
+        stage[p] = s;
+        stage[32 + p] = l;
+        stage[64 + p] = td;
+    }
+    __syncwarp();
+    const bool lst = lane < c;
+    const int cs = lst ? stage[lane] : 0;
+    const int cl = lst ? stage[32 + lane] : 0;
+    const int ctd = stage[64 + (lst ? lane : 0)];  // lanes past the lists alias list 0's table
+    __syncwarp();
+    const int P = warp_incl_scan(cl, lane);
+    const int total = __shfl_sync(FULL, P, 31);
+    const int Pex = P - cl;
+    const int bias = cs - Pex;
+    const unsigned le = lanemask_le(lane);
+    uint32_t hits = 0;
+    unsigned* bm = reinterpret_cast<unsigned*>(stage + 160);
+    const bool use_bm = total <= 32 * BITMAP_WORDS;
+    if (use_bm) {
+        bm[lane] = 0u;
+        bm[lane + 32] = 0u;
+        __syncwarp();
+        if (lst) atomicOr(&bm[Pex >> 5], 1u << (Pex & 31));
+        __syncwarp();
+    }
+    int cum = 0;  // list starts before the current step (bitmap path)
+    for (int base = 0; base < total; base += 32 * VC_UNROLL) {
+        int key[VC_UNROLL], kd[VC_UNROLL];
+        uint4 words = make_uint4(0u, 0u, 0u, 0u);
+        if (use_bm) words = *reinterpret_cast<const uint4*>(bm + (base >> 5));
+        const unsigned wq[4] = {words.x, words.y, words.z, words.w};
+#pragma unroll
+        for (int q = 0; q < VC_UNROLL; ++q) {
+            const int b = base + 32 * q;
+            int o;
+            if (use_bm) {
+                o = (cum + __popc(wq[q] & le) - 1) & 31;
+                cum += __popc(wq[q]);
+            } else {
+                o = vc_owner(b, P, Pex, lst, le) & 31;
+            }
+            const int bo = __shfl_sync(FULL, bias, o);
+            kd[q] = __shfl_sync(FULL, ctd, o);
+            const int f = b + lane;
+            key[q] = (f < total) ? __ldg(dag_col + bo + f) : NOKEY;
+        }
+#pragma unroll
+        for (int q = 0; q < VC_UNROLL; ++q) {
+            const int h = bucket_of<HM>(key[q], (kd[q] >> 16) & 31, mult);
+            const int4 b4 = *reinterpret_cast<const int4*>(sm + (kd[q] & 0xffff) + 4 * h);
+            const int hit = match4(b4, key[q]);
+            hits += hit;
+            if (SLOT_HITS && hit) atomicAdd(&stage[128 + ((kd[q] >> 21) & 31)], 1);
+        }
+    }
+    return hits;
 }
 
 // ---- workers -----------------------------------------------------------------
@@ -342,64 +420,84 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
             const int tab_used = __shfl_sync(FULL, FT, p1 - 1), len_used = __shfl_sync(FULL, FL, p1 - 1);
             const int my_tab = area + FT - ft;                  // slots of this lane's table
             const int my_len = area + tab_used + FL - fl;       // its length words
-            for (int t = lane * 4; t < tab_used; t += 128)
-                *reinterpret_cast<int4*>(smem + area + t) = make_int4(EMPTY, EMPTY, EMPTY, EMPTY);
-            for (int t = lane * 4; t < len_used; t += 128)
-                *reinterpret_cast<int4*>(smem + area + tab_used + t) = make_int4(0, 0, 0, 0);
             if (PER_VERTEX) stage[128 + lane] = 0;
-            __syncwarp();
-            // build every table of the pack from the pack's out-lists, one flat array
+            // build every table of the pack from the pack's out-lists, one flat
+            // array; if any key misses its home bucket, rebuild the pack with the
+            // next hash multiplier (up to 4), else probe with overflow chains
             const int kk = in ? k : 0;
             const int K = warp_incl_scan(kk, lane);
             const int Kex = K - kk;
             const int kbias = a - Kex;  // dag_col index of flat out-edge e owned by this lane
             const int E = __shfl_sync(FULL, K, 31);
-            for (int b0 = 0; b0 < E; b0 += 32 * VC_UNROLL) {
-                int key[VC_UNROLL], own[VC_UNROLL];
+            unsigned mult = kHashMult0;
+            bool chained = false;
+            for (int attempt = 0;; ++attempt) {
+                for (int t = lane * 4; t < tab_used; t += 128)
+                    *reinterpret_cast<int4*>(smem + area + t) = make_int4(EMPTY, EMPTY, EMPTY, EMPTY);
+                for (int t = lane * 4; t < len_used; t += 128)
+                    *reinterpret_cast<int4*>(smem + area + tab_used + t) = make_int4(0, 0, 0, 0);
+                __syncwarp();
+                int ovf = 0;
+                for (int b0 = 0; b0 < E; b0 += 32 * VC_UNROLL) {
+                    int key[VC_UNROLL], own[VC_UNROLL];
 #pragma unroll
-                for (int q = 0; q < VC_UNROLL; ++q) {
-                    const int b = b0 + 32 * q;
-                    const int o = vc_owner(b, K, Kex, true, le) & 31;
-                    const int bo = __shfl_sync(FULL, kbias, o);
-                    own[q] = o;
-                    key[q] = (b + lane < E) ? __ldg(dag_col + bo + b + lane) : NOKEY;
-                }
+                    for (int q = 0; q < VC_UNROLL; ++q) {
+                        const int b = b0 + 32 * q;
+                        const int o = vc_owner(b, K, Kex, true, le) & 31;
+                        const int bo = __shfl_sync(FULL, kbias, o);
+                        own[q] = o;
+                        key[q] = (b + lane < E) ? __ldg(dag_col + bo + b + lane) : NOKEY;
+                    }
 #pragma unroll
-                for (int q = 0; q < VC_UNROLL; ++q) {
-                    const int tb = __shfl_sync(FULL, my_tab, own[q]);
-                    const int lw = __shfl_sync(FULL, my_len, own[q]);
-                    const int lg = __shfl_sync(FULL, lgB, own[q]);
-                    if (key[q] >= 0) insert_b4<HM>(smem, tb, lw, lg, key[q]);
+                    for (int q = 0; q < VC_UNROLL; ++q) {
+                        const int tb = __shfl_sync(FULL, my_tab, own[q]);
+                        const int lw = __shfl_sync(FULL, my_len, own[q]);
+                        const int lg = __shfl_sync(FULL, lgB, own[q]);
+                        if (key[q] >= 0) ovf |= insert_b4<HM>(smem, tb, lw, lg, key[q], mult);
+                    }
                 }
+                __syncwarp();
+                if (!__any_sync(FULL, ovf)) break;
+                if (HM == 1 || attempt == 3) {
+                    chained = true;
+                    break;
+                }
+                mult = hash_mult(attempt + 1);
             }
-            __syncwarp();
             // probe: chunks of 32 out-edges, bounds of the next chunk prefetched
             uint32_t hits = 0;
-            int s = 0, l = 0, etab = 0, emask = 0, eslot = 0;
+            int s = 0, l = 0, etab = 0, elg = 0, eslot = 0;
             {
                 const int o = vc_owner(0, K, Kex, true, le) & 31;
                 const int bo = __shfl_sync(FULL, kbias, o);
                 etab = __shfl_sync(FULL, my_tab, o);
-                emask = __shfl_sync(FULL, lgB, o);
+                elg = __shfl_sync(FULL, lgB, o);
                 eslot = o;
                 list_bounds(lane < E ? __ldg(dag_col + bo + lane) : -1, dag_ptr, n, ctr, s, l);
             }
             for (int c0 = 0; c0 < E; c0 += 32) {
-                int ns = 0, nl = 0, ntab = 0, nmask = 0, nslot = 0;
+                int ns = 0, nl = 0, ntab = 0, nlg = 0, nslot = 0;
                 if (c0 + 32 < E) {
                     const int o = vc_owner(c0 + 32, K, Kex, true, le) & 31;
                     const int bo = __shfl_sync(FULL, kbias, o);
                     ntab = __shfl_sync(FULL, my_tab, o);
-                    nmask = __shfl_sync(FULL, lgB, o);
+                    nlg = __shfl_sync(FULL, lgB, o);
                     nslot = o;
                     const int e = c0 + 32 + lane;
                     list_bounds(e < E ? __ldg(dag_col + bo + e) : -1, dag_ptr, n, ctr, ns, nl);
                 }
-                hits += vc_probe_b4<PER_VERTEX, HM>(s, l, etab, emask, eslot, smem, dag_col, lane, stage);
+                if (!chained) {
+                    hits += vc_pack_fast<PER_VERTEX, HM>(s, l, etab | (elg << 16) | (eslot << 21), smem, dag_col,
+                                                         lane, stage, mult);
+                } else {
+                    int done;
+                    hits += vc_range_b4<PER_VERTEX, HM>(s, l, etab, elg, eslot, 0, 0x7fffffff, smem, dag_col, lane,
+                                                        stage, &done, mult);
+                }
                 s = ns;
                 l = nl;
                 etab = ntab;
-                emask = nmask;
+                elg = nlg;
                 eslot = nslot;
             }
             acc += hits;
@@ -416,7 +514,7 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
 
 // Thread-block workers: one block per work item (u, out-neighbours
 // [nb0, nb1)) of a vertex with d+ > T_w; nb1 - nb0 <= item_nbrs <= 1024.
-// smem: stage[nwarps * STAGE_INTS] | S[item_nbrs] | LP[item_nbrs] | table.
+// smem: stage[nwarps * BLOCK_STAGE_INTS] | S[item_nbrs] | LP[item_nbrs] | table.
 // The block loads the item's out-neighbours' list bounds (S = starts, LP =
 // inclusive prefix of lengths) once, builds the table of one part of N+(u),
 // and its warps take pieces of PIECE combined 2-hop indices from a shared
@@ -433,8 +531,8 @@ __global__ void __launch_bounds__(1024, 1)
     __shared__ int s_wsum[32];
     if (ctr->err) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int* stage = smem + w * STAGE_INTS;
-    int* S = smem + nw * STAGE_INTS;
+    int* stage = smem + w * BLOCK_STAGE_INTS;
+    int* S = smem + nw * BLOCK_STAGE_INTS;
     int* LP = S + item_nbrs;
     const int nitems = ctr->n_items;
     unsigned long long acc = 0;
@@ -596,7 +694,7 @@ int pack_table_ints(int max_out_degree, int min_buckets) {
 // Shared-memory ints a thread-block worker has for its table, after the
 // warps' stages and the item's list bounds and prefix.
 int count_block_budget_ints(const CountCfg& cfg) {
-    return cfg.block_smem_bytes / 4 - (cfg.block_threads / 32) * STAGE_INTS - 2 * cfg.item_neighbors;
+    return cfg.block_smem_bytes / 4 - (cfg.block_threads / 32) * BLOCK_STAGE_INTS - 2 * cfg.item_neighbors;
 }
 
 // Largest part of N+(u) whose bucket-of-4 table (B = nextpow2(part) buckets,
@@ -635,7 +733,7 @@ cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t
                          const int2* warp_desc, const int2* items, unsigned long long* per_vertex,
                          const CountCfg& cfg, DevCounters* ctr, cudaStream_t st, long long* launches) {
     *launches += 2;
-    const int table_off = (cfg.block_threads / 32) * STAGE_INTS + 2 * cfg.item_neighbors;
+    const int table_off = (cfg.block_threads / 32) * BLOCK_STAGE_INTS + 2 * cfg.item_neighbors;
     block_kernel(cfg.hash_mode)<<<cfg.block_grid, cfg.block_threads, cfg.block_smem_bytes, st>>>(
         dag_ptr, dag_col, items, per_vertex, ctr, (int)n, table_off, count_block_part_max(cfg), cfg.item_neighbors);
     pack_kernel(per_vertex != nullptr, cfg.hash_mode)<<<cfg.warp_grid, cfg.warps_per_block * 32,
