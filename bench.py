@@ -257,6 +257,62 @@ def measure_serving(T, torch, dev, seconds: float):
     }
 
 
+def time_count(ctx, torch, dev, n, rp, col, reps=10):
+    """Median ms of tc_count_async (orientation + counting) by CUDA events."""
+    out = torch.zeros(1, dtype=torch.int64, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(2):
+        ctx.count_async(n, rp, col, out, err, stream=stream)
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.count_async(n, rp, col, out, err, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    if int(err.item()) != 0:
+        raise SystemExit("counting failed during the reordering study")
+    return statistics.median(ts), int(out.item())
+
+
+def measure_reorder(T, torch, dev, graphs):
+    """Sec. 4.1 study: for each graph, tc_reorder by in-degree and by
+    collective out-degree; the max collision and Eq. 2 cost of 32-bucket
+    tables (x mod 32 and multiplicative), and the counting time under both
+    table hashes, before and after reordering. The count must not change."""
+    rows = []
+    for name, (n, rp, col) in graphs.items():
+        with T.Context(dev.index) as c:
+            variants = [("none", rp, col, 0.0)]
+            for kind, label in ((T.TC_REORDER_INDEGREE, "indegree"), (T.TC_REORDER_COLLECTIVE, "collective")):
+                c.reorder(n, rp, col, kind, relabel=True)  # warm-up
+                torch.cuda.synchronize(dev)
+                t = time.perf_counter()
+                _, rp2, col2 = c.reorder(n, rp, col, kind, relabel=True)
+                variants.append((label, rp2, col2, (time.perf_counter() - t) * 1e3))
+            base = None
+            for label, r, cc, ms_re in variants:
+                d = c.orient(n, r, cc)
+                st = c.dag_stats(d)
+                d.free()
+                row = {"graph": name, "order": label, "reorder_ms": ms_re,
+                       "max_collision_mod32": st["max_collision_mod32"], "phi_mod32": st["phi_mod32"],
+                       "max_collision_mult32": st["max_collision_mult32"], "phi_mult32": st["phi_mult32"]}
+                for hm, key in ((0, "count_ms_mult_hash"), (1, "count_ms_mod_hash")):
+                    with T.Context(dev.index, params=dict(hash_mode=hm)) as ch:
+                        ms, tri = time_count(ch, torch, dev, n, r, cc)
+                    row[key] = ms
+                    base = tri if base is None else base
+                    row["count_equal"] = tri == base
+                rows.append(row)
+                if label != "none":
+                    del r, cc
+    return rows
+
+
 # -------------------------------------------------------------- the arms
 
 def run_gb300(args):
@@ -282,7 +338,8 @@ def run_gb300(args):
     col_h = np.ascontiguousarray(g.col, dtype=np.int32)
     rp = torch.from_numpy(rp_h).to(dev)
     col = torch.from_numpy(col_h).to(dev)
-    params = dict(record_timing=1, shard_count=world, shard_index=rank)
+    from paper_2103_08053_gb300 import shard
+    params = dict(record_timing=1, **shard.shard_params(rank, world))
     ctx = T.Context(local_rank, params=params)
     stream = torch.cuda.current_stream(dev)
 
@@ -323,15 +380,7 @@ def run_gb300(args):
     elapsed_ms = e0.elapsed_time(e1)
     launches = ctx.kernel_launches() - launches0
     tm = ctx.read_timing()
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-        c = torch.tensor([my_count], dtype=torch.int64, device=dev)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        total_count = int(c.item())
-    else:
-        total_count = my_count
+    total_count, elapsed_ms = shard.combine(my_count, elapsed_ms, device=dev)
     ms_per_step = elapsed_ms / args.steps
     value = g.m / (ms_per_step / 1e3)
 
@@ -349,10 +398,7 @@ def run_gb300(args):
         ctx.count_host(g.n, rp_pin.numpy(), col_pin.numpy(), stream=stream)
     torch.cuda.synchronize(dev)
     e2e_ms = (time.perf_counter() - t_e) * 1e3 / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    _, e2e_ms = shard.combine(0, e2e_ms, device=dev)
     ctx.read_timing()
     ctx.close()
 
@@ -399,6 +445,15 @@ def run_gb300(args):
         result["batched"] = measure_batched(T, torch, dev, steps=args.batch_steps)
     if args.serve_seconds > 0:
         result["serving"] = measure_serving(T, torch, dev, args.serve_seconds)
+    if args.reorder:
+        import numpy as np
+
+        import graphgen as G
+        big = G.rmat(22, 16, seed=5)
+        gs = {WORKLOAD["name"]: (g.n, rp, col),
+              "rmat-s22-ef16-seed5": (big.n, torch.from_numpy(big.row_ptr.astype(np.int32)).to(dev),
+                                      torch.from_numpy(np.ascontiguousarray(big.col, dtype=np.int32)).to(dev))}
+        result["reorder_study"] = measure_reorder(T, torch, dev, gs)
     if not args.no_cpu_baseline:
         import oracle
         cores = oracle.max_threads()
@@ -451,6 +506,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", type=int, default=1, help="1: also time the 4096-graph batch (rank 0)")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--reorder", type=int, default=1,
+                    help="1: also run the Sec. 4.1 reordering study (rank 0)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="seconds of Poisson arrivals for the serving measurement (0: skip; the config is 60)")
     args = ap.parse_args()

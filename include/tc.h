@@ -109,12 +109,20 @@ typedef struct {
     int32_t validate;            /* reserved for extra input checks (0) */
     int32_t record_timing;       /* 1: record CUDA events around the kernel phases (tc_read_timing) */
     int32_t hash_mode;           /* 0: multiplicative hashing (default); 1: x mod B, Algorithm 1's hash */
-    int32_t reserved[3];
+    int32_t scalar_loads;        /* 0: warp workers read 2-hop lists as aligned 16-byte quads (default);
+                                    1: one key per lane per load */
+    int32_t reserved[2];
 } tc_params;
 
 /* Per-DAG statistics (tc_dag_stats), all exact:
  * wedges_plus = W+ = sum_u sum_{v in N+(u)} d+(v), the number of hash probes
- * (the oriented "collective degree" of Eq. 2 summed over u). */
+ * (the oriented "collective degree" of Eq. 2 summed over u).
+ * Collision statistics of the paper's warp table (Sec. 3.1: B = 32 buckets),
+ * with buckets unbounded: for each u, the largest number of keys of N+(u)
+ * that share a bucket ("max collision", Sec. 4.1), and Eq. 2's cost
+ * phi = sum_u (sum_{v in N+(u)} d+(v)) * max collision(u); once under
+ * Algorithm 1's hash x mod 32 ("mod32") and once under the multiplicative hash
+ * the counting kernels use, top 5 bits of x * 0x9E3779B1 ("mult32"). */
 typedef struct {
     int64_t n, m;
     int64_t max_out_degree;
@@ -123,6 +131,8 @@ typedef struct {
     int64_t n_block;       /* d+ > warp_max_out_degree */
     int64_t wedges_plus;   /* W+ */
     int64_t wedges_plus_block; /* part of W+ owned by thread-block vertices */
+    int64_t max_collision_mod32, max_collision_mult32;
+    int64_t phi_mod32, phi_mult32;
 } tc_stats;
 
 /* ---- context ------------------------------------------------------------ */
@@ -180,6 +190,35 @@ tc_status tc_count_host(tc_ctx* ctx, const tc_csr* g, uint64_t* count_host, void
 
 /* Exact statistics of an oriented graph (out-degree bins, W+). Blocks. */
 tc_status tc_dag_stats(tc_ctx* ctx, const tc_dag* dag, tc_stats* out, void* stream);
+
+/* ---- reordering (Sec. 4.1) ---------------------------------------------------- */
+
+/* Vertex renumbering heuristics of Sec. 4.1, which place ids that meet in one
+ * hash table next to each other so that they fall into distinct buckets (the
+ * max-collision factor of the cost model, Eq. 2). The triangle count of the
+ * relabelled graph equals the input's. Both are computed on the rank-by-degree
+ * orientation N+ of the input:
+ *   TC_REORDER_INDEGREE   -- new ids in order of in-degree in N+ (how many
+ *                            out-lists hold the vertex), largest first, ties by
+ *                            smaller old id;
+ *   TC_REORDER_COLLECTIVE -- vertices u taken by collective out-degree
+ *                            sum_{v in N+(u)} d+(v), largest first, ties by
+ *                            smaller old id; each member of N+(u) without a
+ *                            new id gets the next one, in ascending old id;
+ *                            vertices in no out-list follow, by old id. */
+#define TC_REORDER_INDEGREE 1
+#define TC_REORDER_COLLECTIVE 2
+
+/* g: device CSR (caller-owned, as for tc_count). new_id: device int32[n],
+ * caller-owned; receives new_id[old]. out: NULL, or a caller-owned device CSR
+ * with the same n, nnz and offset_bits as g and separate row_ptr / col buffers
+ * of that size; receives the relabelled graph: row new_id[u] holds new_id[v]
+ * for the entries v of row u, in the same order. Scratch (about 24 bytes per
+ * vertex plus the oriented graph) is allocated within the context's budget and
+ * freed before return. Blocks on `stream`. TC_ERR_INVALID_ARG: unknown kind or
+ * mismatched out. */
+tc_status tc_reorder(tc_ctx* ctx, const tc_csr* g, int32_t kind, int32_t* new_id, const tc_csr* out,
+                     void* stream);
 
 /* ---- counting without device allocation ------------------------------------- */
 

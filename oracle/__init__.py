@@ -64,6 +64,8 @@ def _lib():
             lib.oracle_count.restype = ctypes.c_uint64
             lib.oracle_count.argtypes = [ctypes.c_int64, I64P, I32P, ctypes.c_int]
             lib.oracle_max_threads.restype = ctypes.c_int
+            lib.oracle_reorder.restype = ctypes.c_int
+            lib.oracle_reorder.argtypes = [ctypes.c_int64, I64P, I32P, ctypes.c_int, I32P]
             _lib_handle = lib
     return _lib_handle
 
@@ -155,3 +157,65 @@ def count(g, threads: int = 0) -> int:
     if t == U64_MAX:
         raise MemoryError("oracle_count: allocation failed")
     return int(t)
+
+
+REORDER_INDEGREE = 1
+REORDER_COLLECTIVE = 2
+
+
+def reorder(g, kind: int) -> np.ndarray:
+    """new_id[old] of the Sec. 4.1 reordering ``kind`` (1: by in-degree in
+    N+; 2: neighbours of the largest collective out-degree first), computed on
+    the rank-by-degree orientation of g."""
+    d = orient(g)
+    dp, dc = _dag_arrays(d)
+    new_id = np.zeros(max(g.n, 1), dtype=np.int32)
+    if _lib().oracle_reorder(g.n, dp.ctypes.data_as(I64P), dc.ctypes.data_as(I32P), int(kind),
+                             new_id.ctypes.data_as(I32P)) != 0:
+        raise ValueError(f"oracle_reorder failed (kind {kind})")
+    return new_id[:g.n]
+
+
+def relabel(g, new_id):
+    """The CSR of g with vertex old renamed new_id[old]: row new_id[u] holds
+    new_id[v] for the v of row u, in the same order."""
+    from types import SimpleNamespace
+    new_id = np.asarray(new_id, dtype=np.int64)
+    deg = np.diff(np.asarray(g.row_ptr, dtype=np.int64))
+    new_deg = np.zeros(g.n, dtype=np.int64)
+    new_deg[new_id] = deg
+    rp = np.zeros(g.n + 1, dtype=np.int64)
+    np.cumsum(new_deg, out=rp[1:])
+    col = np.zeros(g.nnz, dtype=np.int32)
+    src = np.asarray(g.col, dtype=np.int64)
+    for u in range(g.n):
+        a, b = int(g.row_ptr[u]), int(g.row_ptr[u + 1])
+        w = int(rp[new_id[u]])
+        col[w:w + (b - a)] = new_id[src[a:b]]
+    return SimpleNamespace(n=g.n, nnz=g.nnz, row_ptr=rp, col=col)
+
+
+def collision_stats(d: Dag, hash_kind: str):
+    """(max collision, phi) of 32-bucket tables of every N+(u), buckets
+    unbounded (Sec. 4.1, Eq. 2): hash_kind "mod32" is Algorithm 1's x mod 32,
+    "mult32" the top 5 bits of x * 2654435761 mod 2^32 (multiplicative
+    hashing by 2^32 / golden ratio). phi = sum_u coll(u) * maxload(u), coll(u)
+    the collective out-degree sum_{v in N+(u)} d+(v)."""
+    dp = np.asarray(d.dag_ptr, dtype=np.int64)
+    dc = np.asarray(d.dag_col, dtype=np.int64)
+    dplus = np.diff(dp)
+    mx, phi = 0, 0
+    for u in range(d.n):
+        nu = dc[dp[u]:dp[u + 1]]
+        if nu.size == 0:
+            continue
+        if hash_kind == "mod32":
+            b = nu % 32
+        elif hash_kind == "mult32":
+            b = ((nu * 2654435761) % (1 << 32)) >> 27
+        else:
+            raise ValueError(hash_kind)
+        load = int(np.bincount(b, minlength=32).max())
+        mx = max(mx, load)
+        phi += int(dplus[nu].sum()) * load
+    return mx, phi

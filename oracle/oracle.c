@@ -185,6 +185,80 @@ uint64_t oracle_count(int64_t n, const int64_t* row_ptr, const int32_t* col, int
     return t;
 }
 
+/* ------------------------------------------------------------- reordering */
+
+/* The two vertex reorderings of Sec. 4.1, which change vertex ids (and so the
+ * buckets ids hash to) but never the count. Both run on the oriented graph
+ * N+ (rows sorted ascending, as oracle_orient leaves them):
+ *   kind 1, by in-degree: sort the vertices by in-degree in N+ (the number of
+ *     lists N+(u) that contain v), largest first, ties by smaller old id, and
+ *     number them 0, 1, 2, ... in that order;
+ *   kind 2, neighbours of the largest collective out-degree first: sort the
+ *     vertices u by sum_{v in N+(u)} d+(v), largest first, ties by smaller old
+ *     id; walk them in that order and give every v of N+(u), taken in
+ *     ascending old id, the next new id unless it has one; vertices that got
+ *     none (they are in no list) follow in ascending old id.
+ * new_id[old] receives the new id. Returns 0, or -1 on a bad kind or when
+ * memory runs out. */
+typedef struct {
+    uint64_t key;
+    int64_t id;
+} key_id;
+
+static int cmp_key_desc_id_asc(const void* a, const void* b) {
+    const key_id* x = (const key_id*)a;
+    const key_id* y = (const key_id*)b;
+    if (x->key != y->key) return x->key > y->key ? -1 : 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+int oracle_reorder(int64_t n, const int64_t* dag_ptr, const int32_t* dag_col, int kind, int32_t* new_id) {
+    if (kind != 1 && kind != 2) return -1;
+    key_id* order = (key_id*)malloc((size_t)(n > 0 ? n : 1) * sizeof(key_id));
+    if (!order) return -1;
+    for (int64_t u = 0; u < n; u++) {
+        order[u].id = u;
+        order[u].key = 0;
+    }
+    if (kind == 1) {
+        for (int64_t e = 0; e < dag_ptr[n]; e++) order[dag_col[e]].key++;
+    } else {
+        for (int64_t u = 0; u < n; u++)
+            for (int64_t e = dag_ptr[u]; e < dag_ptr[u + 1]; e++) {
+                int64_t v = dag_col[e];
+                order[u].key += (uint64_t)(dag_ptr[v + 1] - dag_ptr[v]);
+            }
+    }
+    qsort(order, (size_t)n, sizeof(key_id), cmp_key_desc_id_asc);
+    if (kind == 1) {
+        for (int64_t r = 0; r < n; r++) new_id[order[r].id] = (int32_t)r;
+        free(order);
+        return 0;
+    }
+    int64_t max_d = 0;
+    for (int64_t u = 0; u < n; u++)
+        if (dag_ptr[u + 1] - dag_ptr[u] > max_d) max_d = dag_ptr[u + 1] - dag_ptr[u];
+    int32_t* list = (int32_t*)malloc((size_t)(max_d > 0 ? max_d : 1) * sizeof(int32_t));
+    if (!list) {
+        free(order);
+        return -1;
+    }
+    for (int64_t v = 0; v < n; v++) new_id[v] = -1;
+    int64_t next = 0;
+    for (int64_t r = 0; r < n; r++) {
+        int64_t u = order[r].id, d = dag_ptr[u + 1] - dag_ptr[u];
+        memcpy(list, dag_col + dag_ptr[u], (size_t)d * sizeof(int32_t));
+        qsort(list, (size_t)d, sizeof(int32_t), cmp_i32);
+        for (int64_t k = 0; k < d; k++)
+            if (new_id[list[k]] < 0) new_id[list[k]] = (int32_t)next++;
+    }
+    for (int64_t v = 0; v < n; v++)
+        if (new_id[v] < 0) new_id[v] = (int32_t)next++;
+    free(list);
+    free(order);
+    return 0;
+}
+
 int oracle_max_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -12,7 +12,7 @@ import ctypes
 import numpy as np
 
 from . import _tc
-from ._tc import (TC_ERR_BAD_GRAPH, TC_ERR_BUSY, TC_ERR_CUDA, TC_ERR_INVALID_ARG, TC_ERR_NOT_READY, TC_ERR_OOM,
+from ._tc import (TC_REORDER_COLLECTIVE, TC_REORDER_INDEGREE, TC_ERR_BAD_GRAPH, TC_ERR_BUSY, TC_ERR_CUDA, TC_ERR_INVALID_ARG, TC_ERR_NOT_READY, TC_ERR_OOM,
                   TC_ERR_TIMEOUT, TC_ERR_UNSUPPORTED, TC_OK, tc_csr, tc_dag, tc_params, tc_stats, tc_timing)
 
 __all__ = ["Context", "TcError", "Dag", "default_params", "tc_csr", "tc_dag", "tc_params", "tc_stats"]
@@ -191,6 +191,23 @@ class Context:
         s = tc_stats()
         self._check(_tc.tc_dag_stats(self.handle, ctypes.byref(d), ctypes.byref(s), _stream_handle(stream)))
         return {f: int(getattr(s, f)) for f, _ in tc_stats._fields_}
+
+    def reorder(self, n: int, row_ptr, col, kind: int, relabel: bool = True, stream=None):
+        """tc_reorder (Sec. 4.1): new_id (device int32[n]) and, with relabel,
+        the relabelled CSR (row_ptr, col) as new device tensors."""
+        import torch
+        dev = col.device
+        new_id = torch.empty(max(int(n), 1), dtype=torch.int32, device=dev)
+        g = make_csr(n, row_ptr, col)
+        out = None
+        if relabel:
+            rp2 = torch.empty_like(row_ptr)
+            col2 = torch.empty_like(col)
+            out = make_csr(n, rp2, col2)
+        self._check(_tc.tc_reorder(self.handle, ctypes.byref(g), int(kind), ctypes.c_void_p(_ptr(new_id)),
+                                   ctypes.byref(out) if out is not None else None, _stream_handle(stream)))
+        new_id = new_id[:int(n)]
+        return (new_id, rp2, col2) if relabel else new_id
 
     # diagnostics
     def read_timing(self) -> dict:

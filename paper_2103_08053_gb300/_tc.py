@@ -36,6 +36,10 @@ TC_ERR_TIMEOUT = 6
 TC_ERR_CUDA = 7
 TC_ERR_UNSUPPORTED = 8
 
+# tc_reorder kinds
+TC_REORDER_INDEGREE = 1
+TC_REORDER_COLLECTIVE = 2
+
 
 class tc_csr(ctypes.Structure):
     _fields_ = [("n", c_int64), ("nnz", c_int64), ("row_ptr", c_void_p), ("offset_bits", c_int32),
@@ -51,7 +55,8 @@ class tc_params(ctypes.Structure):
                 ("block_threads", c_int32), ("block_smem_bytes", c_int32),
                 ("item_neighbors", c_int32), ("chunk", c_int32), ("warps_per_block", c_int32),
                 ("shard_count", c_int32), ("shard_index", c_int32), ("validate", c_int32),
-                ("record_timing", c_int32), ("hash_mode", c_int32), ("reserved", c_int32 * 3)]
+                ("record_timing", c_int32), ("hash_mode", c_int32), ("scalar_loads", c_int32),
+                ("reserved", c_int32 * 2)]
 
 
 class tc_timing(ctypes.Structure):
@@ -62,7 +67,9 @@ class tc_timing(ctypes.Structure):
 class tc_stats(ctypes.Structure):
     _fields_ = [("n", c_int64), ("m", c_int64), ("max_out_degree", c_int64), ("n_skip", c_int64),
                 ("n_warp", c_int64), ("n_block", c_int64), ("wedges_plus", c_int64),
-                ("wedges_plus_block", c_int64)]
+                ("wedges_plus_block", c_int64),
+                ("max_collision_mod32", c_int64), ("max_collision_mult32", c_int64),
+                ("phi_mod32", c_int64), ("phi_mult32", c_int64)]
 
 
 _P = ctypes.POINTER
@@ -88,6 +95,7 @@ _protos = {
     "tc_drain": (c_int32, [c_void_p]),
     "tc_read_timing": (c_int32, [c_void_p, _P(tc_timing)]),
     "tc_count_dag_noalloc": (c_int32, [_P(tc_dag), c_void_p, c_void_p, c_void_p]),
+    "tc_reorder": (c_int32, [c_void_p, _P(tc_csr), c_int32, c_void_p, _P(tc_csr), c_void_p]),
     "tc_kernel_launches": (c_int32, [c_void_p, _P(c_int64)]),
     "tc_status_string": (ctypes.c_char_p, [c_int32]),
     "tc_last_error": (ctypes.c_char_p, [c_void_p]),

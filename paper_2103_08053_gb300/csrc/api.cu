@@ -126,6 +126,7 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         p.validate = in->validate;
         p.record_timing = in->record_timing;
         p.hash_mode = in->hash_mode;
+        p.scalar_loads = in->scalar_loads;
 #undef TAKE
     }
     if (p.warp_max_out_degree < 1 || p.warp_max_out_degree > 255)
@@ -148,6 +149,8 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
     if (p.item_neighbors < 32 || p.item_neighbors > p.block_threads || p.item_neighbors % 32)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "item_neighbors must be a multiple of 32 in [32, block_threads]");
     if (p.hash_mode != 0 && p.hash_mode != 1) return ctx_fail(ctx, TC_ERR_INVALID_ARG, "hash_mode must be 0 or 1");
+    if (p.scalar_loads != 0 && p.scalar_loads != 1)
+        return ctx_fail(ctx, TC_ERR_INVALID_ARG, "scalar_loads must be 0 or 1");
     if (p.chunk < 1 || p.chunk > 32) return ctx_fail(ctx, TC_ERR_INVALID_ARG, "chunk must be in [1, 32]");
     if (p.shard_count < 1 || p.shard_index < 0 || p.shard_index >= p.shard_count)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "need 0 <= shard_index < shard_count");
@@ -158,7 +161,7 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "warp kernel needs %lld B of shared memory (max %d)", warp_smem,
                         max_smem);
     if (p.block_smem_bytes > max_smem || p.block_smem_bytes % 16 ||
-        p.block_smem_bytes / 4 - (p.block_threads / 32) * 128 - 2 * p.item_neighbors < 5 * 64)
+        p.block_smem_bytes / 4 - (p.block_threads / 32) * 128 - 3 * p.item_neighbors < 5 * 64)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "block_smem_bytes out of range (max %d)", max_smem);
     if (out) *out = p;
     if (cfg) {
@@ -174,6 +177,7 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         cfg->shard_index = p.shard_index;
         cfg->record_timing = p.record_timing ? 1 : 0;
         cfg->hash_mode = p.hash_mode;
+        cfg->quad_loads = p.scalar_loads ? 0 : 1;
         cfg->warp_grid = cfg->block_grid = 0;
     }
     return TC_OK;
@@ -283,6 +287,19 @@ static tc_status read_counters(tc_ctx* ctx, Workspace& ws, cudaStream_t st, DevC
     *out = *ctx->host_ctr;
     if (out->err) return ctx_fail(ctx, err_bits_status(out->err), "%s", err_bits_text(out->err));
     return TC_OK;
+}
+
+tc_status tcg::orient_to_workspace(tc_ctx* ctx, const tc_csr* g, cudaStream_t st, int64_t* m) {
+    Workspace& ws = ctx->ws;
+    tc_status s = ensure_orient_ws(ctx, ws, g->n, g->nnz, st);
+    if (!s) s = ws.dag_ptr.ensure(ctx, (size_t)(g->n + 1) * 4, st);
+    if (!s) s = ws.dag_col.ensure(ctx, (size_t)(g->nnz / 2 + 1) * 4, st);
+    if (!s) s = cuda_status(ctx, cudaMemsetAsync(ws.ctr.p, 0, sizeof(DevCounters), st), "memset counters");
+    if (!s) s = enqueue_orient(ctx, ws, g, (int32_t*)ws.dag_ptr.p, (int32_t*)ws.dag_col.p, g->nnz / 2 + 1, st);
+    DevCounters c;
+    if (!s) s = read_counters(ctx, ws, st, &c);
+    if (!s) *m = c.m;
+    return s;
 }
 
 // ------------------------------------------------------------------ C ABI
@@ -546,6 +563,10 @@ tc_status tc_dag_stats(tc_ctx* ctx, const tc_dag* dag, tc_stats* out, void* stre
     out->n_block = h.n_block;
     out->wedges_plus = (int64_t)h.wplus;
     out->wedges_plus_block = (int64_t)h.wplus_block;
+    out->max_collision_mod32 = h.maxc[0];
+    out->max_collision_mult32 = h.maxc[1];
+    out->phi_mod32 = (int64_t)h.phi[0];
+    out->phi_mult32 = (int64_t)h.phi[1];
     return TC_OK;
 }
 

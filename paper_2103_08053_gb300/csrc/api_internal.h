@@ -123,6 +123,8 @@ tc_status resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, Count
 tc_status check_csr(tc_ctx* ctx, const tc_csr* g);
 tc_status ensure_count_ws(tc_ctx* ctx, Workspace& ws, int64_t n, int64_t m, cudaStream_t st);
 tc_status ensure_orient_ws(tc_ctx* ctx, Workspace& ws, int64_t n, int64_t nnz, cudaStream_t st);
+// Orient g into ctx->ws.dag_ptr / dag_col (blocking on st); *m = DAG edges.
+tc_status orient_to_workspace(tc_ctx* ctx, const tc_csr* g, cudaStream_t st, int64_t* m);
 
 void batch_release(tc_ctx* ctx);  // batch.cu
 size_t noalloc_scratch_bytes();    // noalloc.cu

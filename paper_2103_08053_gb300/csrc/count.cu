@@ -340,6 +340,202 @@ __device__ __forceinline__ uint32_t vc_pack_fast(int s, int l, int td, const int
     return hits;
 }
 
+// Quad-vectorised variant of vc_pack_fast. The 2-hop lists are read as
+// aligned 16-byte quads of dag_col: list [s, e) covers the quads
+// [s >> 2, (e + 3) >> 2), the quads of all lists are combined virtually and
+// dealt one per lane, so each lane loads four keys with one 16-byte load and
+// a warp reads 512 contiguous bytes of a long list; the slots of a quad that
+// lie outside [s, e) are masked. This divides the owner search, the two
+// shuffles and the address arithmetic of a probe by up to four. dag_col must
+// be 16-byte aligned; m = dag_ptr[n] is the number of readable entries, and a
+// quad that reaches past it is read entry by entry. Owners: bitmap of list
+// starts in quad space when the lists span <= BITMAP_WORDS * 32 quads, else
+// vc_owner.
+constexpr int QUAD_UNROLL = 2;  // quads in flight per lane
+template <bool SLOT_HITS, int HM>
+__device__ __forceinline__ uint32_t vc_pack_quad(int s, int l, int td, const int* sm,
+                                                 const int32_t* __restrict__ dag_col, int m, int lane, int* stage,
+                                                 unsigned mult) {
+    const unsigned nem = __ballot_sync(FULL, l > 0);
+    if (nem == 0) return 0;
+    const int c = __popc(nem);
+    if (l > 0) {
+        const int p = __popc(nem & lanemask_lt(lane));
+        stage[p] = s;
+        stage[32 + p] = s + l;
+        stage[64 + p] = td;
+    }
+    __syncwarp();
+    const bool lst = lane < c;
+    const int cs = lst ? stage[lane] : 0;
+    const int ce = lst ? stage[32 + lane] : 0;
+    const int ctd = stage[64 + (lst ? lane : 0)];  // lanes past the lists alias list 0's table
+    __syncwarp();
+    const int nq = lst ? ((ce + 3) >> 2) - (cs >> 2) : 0;
+    const int P = warp_incl_scan(nq, lane);
+    const int total = __shfl_sync(FULL, P, 31);
+    const int Pex = P - nq;
+    const int qbias = (cs >> 2) - Pex;  // global quad index of combined quad f of this list: qbias + f
+    const unsigned le = lanemask_le(lane);
+    uint32_t hits = 0;
+    unsigned* bm = reinterpret_cast<unsigned*>(stage + 160);
+    const bool use_bm = total <= 32 * BITMAP_WORDS;
+    if (use_bm) {
+        bm[lane] = 0u;
+        bm[lane + 32] = 0u;
+        __syncwarp();
+        if (lst) atomicOr(&bm[Pex >> 5], 1u << (Pex & 31));
+        __syncwarp();
+    }
+    const int4* __restrict__ quads = reinterpret_cast<const int4*>(dag_col);
+    int cum = 0;
+    for (int base = 0; base < total; base += 32 * QUAD_UNROLL) {
+        int4 v[QUAD_UNROLL];
+        int lo[QUAD_UNROLL], hi[QUAD_UNROLL], kd[QUAD_UNROLL];
+        uint2 words = make_uint2(0u, 0u);
+        if (use_bm) words = *reinterpret_cast<const uint2*>(bm + (base >> 5));
+        const unsigned wq[2] = {words.x, words.y};
+#pragma unroll
+        for (int q = 0; q < QUAD_UNROLL; ++q) {
+            const int b = base + 32 * q;
+            int o;
+            if (use_bm) {
+                o = (cum + __popc(wq[q] & le) - 1) & 31;
+                cum += __popc(wq[q]);
+            } else {
+                o = vc_owner(b, P, Pex, lst, le) & 31;
+            }
+            const int qb = __shfl_sync(FULL, qbias, o);
+            const int so = __shfl_sync(FULL, cs, o);
+            const int eo = __shfl_sync(FULL, ce, o);
+            kd[q] = __shfl_sync(FULL, ctd, o);
+            const int f = b + lane;
+            const int x0 = 4 * (qb + f);  // dag_col index of the quad's first slot
+            v[q] = make_int4(NOKEY, NOKEY, NOKEY, NOKEY);
+            if (f < total) {
+                lo[q] = so - x0;
+                hi[q] = eo - x0;
+                if (x0 + 3 < m) {
+                    v[q] = __ldg(quads + (qb + f));
+                } else {
+                    if (x0 < m) v[q].x = __ldg(dag_col + x0);
+                    if (x0 + 1 < m) v[q].y = __ldg(dag_col + x0 + 1);
+                    if (x0 + 2 < m) v[q].z = __ldg(dag_col + x0 + 2);
+                }
+            } else {
+                lo[q] = 4;
+                hi[q] = 0;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < QUAD_UNROLL; ++q) {
+            const int lg = (kd[q] >> 16) & 31;
+            const int tab = kd[q] & 0xffff;
+            const int key[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+            int hq = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (j >= lo[q] && j < hi[q]) {
+                    const int h = bucket_of<HM>(key[j], lg, mult);
+                    const int4 b4 = *reinterpret_cast<const int4*>(sm + tab + 4 * h);
+                    hq += match4(b4, key[j]);
+                }
+            }
+            hits += hq;
+            if (SLOT_HITS && hq) atomicAdd(&stage[128 + ((kd[q] >> 21) & 31)], hq);
+        }
+    }
+    return hits;
+}
+
+// Quad-vectorised variant of vc_range_b4 for one table (thread-block
+// workers): lane i brings the list dag_col[s, e) with nq quads; the combined
+// quad indices [skip, min(limit, total)) are dealt one per lane, QUAD_UNROLL
+// per step; slots outside their list are masked; a key whose bucket is full
+// and did not match walks the overflow chain. *done = quads processed.
+template <int HM>
+__device__ __forceinline__ uint32_t vc_range_quad(int s, int e, int nq, int tab, int lgB, int skip, int limit,
+                                                  const int* sm, const int32_t* __restrict__ dag_col, int m, int lane,
+                                                  int* stage, int* done) {
+    const unsigned nem = __ballot_sync(FULL, nq > 0);
+    if (nem == 0) {
+        *done = 0;
+        return 0;
+    }
+    const int c = __popc(nem);
+    if (nq > 0) {
+        const int p = __popc(nem & lanemask_lt(lane));
+        stage[p] = s;
+        stage[32 + p] = e;
+        stage[64 + p] = nq;
+    }
+    __syncwarp();
+    const bool lst = lane < c;
+    const int cs = lst ? stage[lane] : 0;
+    const int ce = lst ? stage[32 + lane] : 0;
+    const int cq = lst ? stage[64 + lane] : 0;
+    __syncwarp();
+    const int P = warp_incl_scan(cq, lane);
+    const int total = __shfl_sync(FULL, P, 31);
+    const int end = total < limit ? total : limit;
+    const int Pex = P - cq;
+    const int qbias = (cs >> 2) - Pex;
+    const unsigned le = lanemask_le(lane);
+    const int mask = (1 << lgB) - 1;
+    const int4* __restrict__ quads = reinterpret_cast<const int4*>(dag_col);
+    uint32_t hits = 0;
+    for (int base = skip; base < end; base += 32 * QUAD_UNROLL) {
+        int4 v[QUAD_UNROLL];
+        int lo[QUAD_UNROLL], hi[QUAD_UNROLL];
+#pragma unroll
+        for (int q = 0; q < QUAD_UNROLL; ++q) {
+            const int b = base + 32 * q;
+            const int o = vc_owner(b, P, Pex, lst, le) & 31;
+            const int qb = __shfl_sync(FULL, qbias, o);
+            const int so = __shfl_sync(FULL, cs, o);
+            const int eo = __shfl_sync(FULL, ce, o);
+            const int f = b + lane;
+            const int x0 = 4 * (qb + f);
+            v[q] = make_int4(NOKEY, NOKEY, NOKEY, NOKEY);
+            if (f < end) {
+                lo[q] = so - x0;
+                hi[q] = eo - x0;
+                if (x0 + 3 < m) {
+                    v[q] = __ldg(quads + (qb + f));
+                } else {
+                    if (x0 < m) v[q].x = __ldg(dag_col + x0);
+                    if (x0 + 1 < m) v[q].y = __ldg(dag_col + x0 + 1);
+                    if (x0 + 2 < m) v[q].z = __ldg(dag_col + x0 + 2);
+                }
+            } else {
+                lo[q] = 4;
+                hi[q] = 0;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < QUAD_UNROLL; ++q) {
+            const int key[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+            int more = 0;  // bit j: slot j's bucket was full and did not match
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (j >= lo[q] && j < hi[q]) {
+                    const int h = bucket_of<HM>(key[j], lgB);
+                    const int4 b4 = *reinterpret_cast<const int4*>(sm + tab + 4 * h);
+                    const int hit = match4(b4, key[j]);
+                    hits += hit;
+                    more |= (!hit && b4.w != EMPTY) << j;
+                }
+            }
+            if (__any_sync(FULL, more)) {
+                for (int j = 0; j < 4; ++j)
+                    if ((more >> j) & 1) hits += probe_b4_chain(sm, tab, mask, bucket_of<HM>(key[j], lgB), key[j]);
+            }
+        }
+    }
+    *done = end > skip ? end - skip : 0;
+    return hits;
+}
+
 // ---- workers -----------------------------------------------------------------
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
@@ -385,10 +581,11 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
     k_count_pack(const int32_t* __restrict__ dag_ptr, const int32_t* __restrict__ dag_col,
                  const int2* __restrict__ desc, const int32_t* __restrict__ warp_list,
                  unsigned long long* __restrict__ per_vertex, DevCounters* ctr, int n, int area_ints,
-                 int lg_min_buckets, int pop) {
+                 int lg_min_buckets, int pop, int quad) {
     extern __shared__ int smem[];
     if (ctr->err) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int m = quad ? __ldg(dag_ptr + n) : 0;  // readable dag_col entries (quad path)
     const unsigned le = lanemask_le(lane);
     const int area = w * (area_ints + STAGE_INTS);  // int offset of this warp's area in smem
     int* stage = smem + area + area_ints;
@@ -486,7 +683,10 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
                     const int e = c0 + 32 + lane;
                     list_bounds(e < E ? __ldg(dag_col + bo + e) : -1, dag_ptr, n, ctr, ns, nl);
                 }
-                if (!chained) {
+                if (!chained && quad) {
+                    hits += vc_pack_quad<PER_VERTEX, HM>(s, l, etab | (elg << 16) | (eslot << 21), smem, dag_col,
+                                                         m, lane, stage, mult);
+                } else if (!chained) {
                     hits += vc_pack_fast<PER_VERTEX, HM>(s, l, etab | (elg << 16) | (eslot << 21), smem, dag_col,
                                                          lane, stage, mult);
                 } else {
@@ -525,15 +725,17 @@ template <int PIECE, int HM>
 __global__ void __launch_bounds__(1024, 1)
     k_count_block(const int32_t* __restrict__ dag_ptr, const int32_t* __restrict__ dag_col,
                   const int2* __restrict__ items, unsigned long long* __restrict__ per_vertex, DevCounters* ctr,
-                  int n, int table_off, int part_max, int item_nbrs) {
+                  int n, int table_off, int part_max, int item_nbrs, int quad) {
     extern __shared__ int smem[];
     __shared__ int s_item, s_piece;
     __shared__ int s_wsum[32];
     if (ctr->err) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int m = quad ? __ldg(dag_ptr + n) : 0;  // readable dag_col entries (quad path)
     int* stage = smem + w * BLOCK_STAGE_INTS;
     int* S = smem + nw * BLOCK_STAGE_INTS;
-    int* LP = S + item_nbrs;
+    int* E = S + item_nbrs;
+    int* LP = E + item_nbrs;
     const int nitems = ctr->n_items;
     unsigned long long acc = 0;
     for (;;) {
@@ -550,7 +752,9 @@ __global__ void __launch_bounds__(1024, 1)
         // list bounds of the item's out-neighbours, and the block-wide prefix of their lengths
         int ls = 0, ll = 0;
         if ((int)threadIdx.x < cnt) list_bounds(__ldg(dag_col + a + nb0 + threadIdx.x), dag_ptr, n, ctr, ls, ll);
-        const int wi = warp_incl_scan(ll, lane);
+        // quad path: the prefix counts the quads each list spans
+        const int units = (quad && ll > 0) ? ((ls + ll + 3) >> 2) - (ls >> 2) : ll;
+        const int wi = warp_incl_scan(units, lane);
         if (lane == 31) s_wsum[w] = wi;
         __syncthreads();
         if (w == 0) {
@@ -560,6 +764,7 @@ __global__ void __launch_bounds__(1024, 1)
         __syncthreads();
         if ((int)threadIdx.x < cnt) {
             S[threadIdx.x] = ls;
+            E[threadIdx.x] = ls + ll;
             LP[threadIdx.x] = s_wsum[w] + wi;
         }
         __syncthreads();
@@ -579,13 +784,14 @@ __global__ void __launch_bounds__(1024, 1)
             for (int t = threadIdx.x; t < pk; t += blockDim.x)
                 insert_b4w<HM>(smem, table_off, lenw, lgB, __ldg(dag_col + a + p0 + t));
             __syncthreads();
+            const int piece = quad ? PIECE / 4 : PIECE;  // combined units (quads or keys) per piece
             for (;;) {
                 int pc = 0;
                 if (lane == 0) pc = atomicAdd(&s_piece, 1);
                 pc = __shfl_sync(FULL, pc, 0);
-                int F = pc * PIECE;
+                int F = pc * piece;
                 if (F >= W) break;
-                const int F1 = min(W, F + PIECE);
+                const int F1 = min(W, F + piece);
                 while (F < F1) {
                     // j0 = first list with LP[j0] > F (cnt <= 1024: two 32-ary rounds)
                     const int i1 = min(cnt - 1, lane * 32 + 31);
@@ -593,12 +799,18 @@ __global__ void __launch_bounds__(1024, 1)
                     const int i2 = blk * 32 + lane;
                     const int j0 = blk * 32 + __popc(__ballot_sync(FULL, i2 < cnt && LP[i2] <= F));
                     const int j = j0 + lane;
-                    const int lj = j < cnt ? LP[j] - (j ? LP[j - 1] : 0) : 0;
+                    const int uj = j < cnt ? LP[j] - (j ? LP[j - 1] : 0) : 0;
                     const int sj = j < cnt ? S[j] : 0;
                     const int base_flat = j0 ? LP[j0 - 1] : 0;
                     int done = 0;
-                    h += vc_range_b4<false, HM>(sj, lj, table_off, lgB, 0, F - base_flat, F1 - base_flat, smem,
-                                            dag_col, lane, stage, &done);
+                    if (quad) {
+                        const int ej = j < cnt ? E[j] : 0;
+                        h += vc_range_quad<HM>(sj, ej, uj, table_off, lgB, F - base_flat, F1 - base_flat, smem,
+                                               dag_col, m, lane, stage, &done);
+                    } else {
+                        h += vc_range_b4<false, HM>(sj, uj, table_off, lgB, 0, F - base_flat, F1 - base_flat, smem,
+                                                    dag_col, lane, stage, &done);
+                    }
                     F += done;
                 }
             }
@@ -662,10 +874,57 @@ __global__ void k_stats(const int32_t* __restrict__ dag_ptr, const int32_t* __re
     }
 }
 
+// Collision statistics of 32-bucket tables, one warp per vertex u: per
+// bucket, the number of keys of N+(u) it receives (x mod 32, and the top 5
+// bits of x * kHashMult0), counted with shared-memory atomics; the largest
+// count is u's max collision, and Eq. 2's phi adds the collective out-degree
+// of u times it. Launched with 256 threads per block.
+__global__ void __launch_bounds__(256) k_collision(const int32_t* __restrict__ dag_ptr,
+                                                   const int32_t* __restrict__ dag_col, int64_t n, DevStats* out) {
+    __shared__ int cnt[8][2][32];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    long long mx0 = 0, mx1 = 0;
+    unsigned long long phi0 = 0, phi1 = 0;
+    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+        const int a = dag_ptr[u], b = dag_ptr[u + 1];
+        if (b == a) continue;
+        cnt[wl][0][lane] = 0;
+        cnt[wl][1][lane] = 0;
+        __syncwarp();
+        unsigned long long coll = 0;
+        for (int e = a + lane; e < b; e += 32) {
+            const int w = dag_col[e];
+            coll += (unsigned)(dag_ptr[w + 1] - dag_ptr[w]);
+            atomicAdd(&cnt[wl][0][w & 31], 1);
+            atomicAdd(&cnt[wl][1][((unsigned)w * kHashMult0) >> 27], 1);
+        }
+        __syncwarp();
+        coll = warp_sum_u64(coll);
+        int m0 = cnt[wl][0][lane], m1 = cnt[wl][1][lane];
+        __syncwarp();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            m0 = max(m0, __shfl_xor_sync(FULL, m0, o));
+            m1 = max(m1, __shfl_xor_sync(FULL, m1, o));
+        }
+        mx0 = max(mx0, (long long)m0);
+        mx1 = max(mx1, (long long)m1);
+        phi0 += coll * (unsigned)m0;
+        phi1 += coll * (unsigned)m1;
+    }
+    if (lane == 0) {
+        atomicMax(&out->maxc[0], mx0);
+        atomicMax(&out->maxc[1], mx1);
+        atomicAdd(&out->phi[0], phi0);
+        atomicAdd(&out->phi[1], phi1);
+    }
+}
+
 int pack_smem_bytes(const CountCfg& cfg) { return cfg.warps_per_block * (cfg.warp_area_ints + STAGE_INTS) * 4; }
 
 using PackKernel = void (*)(const int32_t*, const int32_t*, const int2*, const int32_t*, unsigned long long*,
-                            DevCounters*, int, int, int, int);
+                            DevCounters*, int, int, int, int, int);
 
 PackKernel pack_kernel(bool per_vertex, int hm) {
     if (hm == 1) return per_vertex ? k_count_pack<true, 1> : k_count_pack<false, 1>;
@@ -673,7 +932,7 @@ PackKernel pack_kernel(bool per_vertex, int hm) {
 }
 
 using BlockKernel = void (*)(const int32_t*, const int32_t*, const int2*, unsigned long long*, DevCounters*, int,
-                             int, int, int);
+                             int, int, int, int);
 
 BlockKernel block_kernel(int hm) { return hm == 1 ? k_count_block<BLOCK_PIECE, 1> : k_count_block<BLOCK_PIECE, 0>; }
 
@@ -694,7 +953,7 @@ int pack_table_ints(int max_out_degree, int min_buckets) {
 // Shared-memory ints a thread-block worker has for its table, after the
 // warps' stages and the item's list bounds and prefix.
 int count_block_budget_ints(const CountCfg& cfg) {
-    return cfg.block_smem_bytes / 4 - (cfg.block_threads / 32) * BLOCK_STAGE_INTS - 2 * cfg.item_neighbors;
+    return cfg.block_smem_bytes / 4 - (cfg.block_threads / 32) * BLOCK_STAGE_INTS - 3 * cfg.item_neighbors;
 }
 
 // Largest part of N+(u) whose bucket-of-4 table (B = nextpow2(part) buckets,
@@ -733,13 +992,15 @@ cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t
                          const int2* warp_desc, const int2* items, unsigned long long* per_vertex,
                          const CountCfg& cfg, DevCounters* ctr, cudaStream_t st, long long* launches) {
     *launches += 2;
-    const int table_off = (cfg.block_threads / 32) * BLOCK_STAGE_INTS + 2 * cfg.item_neighbors;
+    const int table_off = (cfg.block_threads / 32) * BLOCK_STAGE_INTS + 3 * cfg.item_neighbors;
+    const int quad = (cfg.quad_loads && ((uintptr_t)dag_col & 15) == 0) ? 1 : 0;
     block_kernel(cfg.hash_mode)<<<cfg.block_grid, cfg.block_threads, cfg.block_smem_bytes, st>>>(
-        dag_ptr, dag_col, items, per_vertex, ctr, (int)n, table_off, count_block_part_max(cfg), cfg.item_neighbors);
+        dag_ptr, dag_col, items, per_vertex, ctr, (int)n, table_off, count_block_part_max(cfg), cfg.item_neighbors,
+        quad);
     pack_kernel(per_vertex != nullptr, cfg.hash_mode)<<<cfg.warp_grid, cfg.warps_per_block * 32,
                                                       pack_smem_bytes(cfg), st>>>(
         dag_ptr, dag_col, warp_desc, warp_list, per_vertex, ctr, (int)n, cfg.warp_area_ints,
-        lg2(cfg.warp_min_buckets), cfg.chunk);
+        lg2(cfg.warp_min_buckets), cfg.chunk, quad);
     return cudaGetLastError();
 }
 
@@ -756,6 +1017,7 @@ cudaError_t launch_stats(const int32_t* dag_ptr, const int32_t* dag_col, int64_t
     int g = (int)((n + 255) / 256);
     if (g > 4096) g = 4096;
     k_stats<<<g, 256, 0, st>>>(dag_ptr, dag_col, n, warp_max_out_degree, out);
+    k_collision<<<g, 256, 0, st>>>(dag_ptr, dag_col, n, out);
     return cudaGetLastError();
 }
 

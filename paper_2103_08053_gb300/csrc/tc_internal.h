@@ -49,6 +49,7 @@ struct CountCfg {
     int shard_count, shard_index;
     int record_timing;
     int hash_mode;  // 0 multiplicative, 1 x mod B
+    int quad_loads; // 1: warp workers read 2-hop lists as 16-byte quads (when dag_col is 16-byte aligned)
 };
 
 // One graph of an orientation pass. A batch places its graphs in one padded
@@ -102,6 +103,8 @@ struct DevStats {
     unsigned long long wplus, wplus_block;
     long long max_out;
     long long n_skip, n_warp, n_block;
+    long long maxc[2];           // max collision, B = 32: [0] x mod 32, [1] multiplicative
+    unsigned long long phi[2];   // Eq. 2 cost with the same tables
 };
 cudaError_t launch_stats(const int32_t* dag_ptr, const int32_t* dag_col, int64_t n, int warp_max_out_degree,
                          DevStats* out, cudaStream_t st);

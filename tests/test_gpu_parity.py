@@ -155,6 +155,39 @@ def test_per_vertex_counts(ctx):
     d.free()
 
 
+def test_unaligned_dag_and_ragged_quads(ctx):
+    # 16-byte quad loads need an aligned dag_col; a DAG whose dag_col starts 4
+    # bytes past an alignment boundary is probed one key per lane. Both must
+    # equal the oracle, including the per-vertex counts, and so must a DAG
+    # whose last list ends at a length that is not a multiple of 4.
+    g = G.rmat(12, 12, seed=21)
+    od = oracle.orient(g)
+    want_total, want_pv = oracle.count_dag(od, per_vertex=True)
+    dp = torch.from_numpy(od.dag_ptr.astype(np.int32)).cuda()
+    for shift in (0, 1, 2, 3):
+        buf = torch.zeros(od.m + 4, dtype=torch.int32, device="cuda")
+        buf[shift:shift + od.m] = torch.from_numpy(od.dag_col).cuda()
+        dc = buf[shift:shift + od.m]
+        raw = T_tc().tc_dag(g.n, od.m, dp.data_ptr(), dc.data_ptr())
+        pv = torch.zeros(g.n, dtype=torch.int64, device="cuda")
+        assert ctx.count_dag(raw, per_vertex=pv) == want_total
+        assert np.array_equal(pv.cpu().numpy().astype(np.uint64), want_pv)
+    # a DAG cut right after a list whose end is not quad-aligned
+    cut = next(u for u in range(g.n, 0, -1) if od.dag_ptr[u] % 4 != 0 and od.dag_ptr[u] > 0)
+    sub_ptr = np.minimum(od.dag_ptr, od.dag_ptr[cut])
+    sub = oracle.Dag(g.n, sub_ptr, od.dag_col[:od.dag_ptr[cut]].copy())
+    exact = torch.from_numpy(sub.dag_col).cuda().clone()   # allocation of exactly m entries
+    dps = torch.from_numpy(sub_ptr.astype(np.int32)).cuda()
+    raw = T_tc().tc_dag(g.n, sub.m, dps.data_ptr(), exact.data_ptr())
+    # keys in the truncated lists may name vertices >= cut whose lists are now empty
+    assert ctx.count_dag(raw) == oracle.count_dag(sub)
+
+
+def T_tc():
+    from paper_2103_08053_gb300 import _tc
+    return _tc
+
+
 # ------------------------------------------------------ worker/table regimes
 
 PARAM_SETS = {
@@ -169,6 +202,7 @@ PARAM_SETS = {
     # ^ part_max = 256: out-lists longer than 256 are probed part by part
     "chunk7": dict(chunk=7, warp_area_ints=4608),
     "paper_hash": dict(hash_mode=1),
+    "scalar_loads": dict(scalar_loads=1),                      # one 2-hop key per lane per load
 }
 
 

@@ -256,3 +256,86 @@ def test_gnp_expected_value_smoke():
     ts = [oracle.count(G.erdos_renyi(n, p, seed=1000 + s)) for s in range(8)]
     expect = math.comb(n, 3) * p ** 3
     assert abs(np.mean(ts) - expect) < 4 * 75 / math.sqrt(len(ts))
+
+
+# -------------------------------------------------------------- reordering
+
+def test_reorder_worked_example():
+    ex = json.load(open(os.path.join(GOLDEN, "reorder_example.json")))
+    g = G.from_edge_list(ex["n"], [tuple(e) for e in ex["edges"]])
+    assert np.diff(g.row_ptr).tolist() == ex["degrees"]
+    d = oracle.orient(g)
+    rows = [d.dag_col[d.dag_ptr[u]:d.dag_ptr[u + 1]].tolist() for u in range(g.n)]
+    assert rows == ex["oriented_out_lists"]
+    assert oracle.reorder(g, oracle.REORDER_INDEGREE).tolist() == ex["new_id_indegree"]
+    assert oracle.reorder(g, oracle.REORDER_COLLECTIVE).tolist() == ex["new_id_collective"]
+    for kind in (1, 2):
+        h = oracle.relabel(g, oracle.reorder(g, kind))
+        assert oracle.count(h) == oracle.brute(h) == ex["triangles"]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_reorder_is_a_permutation_and_keeps_the_count(seed):
+    g = G.rmat(9, 6 + seed, seed=300 + seed)
+    want = oracle.count(g)
+    for kind in (oracle.REORDER_INDEGREE, oracle.REORDER_COLLECTIVE):
+        nid = oracle.reorder(g, kind)
+        assert sorted(nid.tolist()) == list(range(g.n))
+        h = oracle.relabel(g, nid)
+        assert oracle.count(h) == want
+        # the relabelled CSR is the same graph as graphgen's relabel builds
+        r = G.relabel(g, nid)
+        for u in range(g.n):
+            a = sorted(h.col[h.row_ptr[u]:h.row_ptr[u + 1]].tolist())
+            b = sorted(r.col[r.row_ptr[u]:r.row_ptr[u + 1]].tolist())
+            assert a == b
+
+
+def test_reorder_indegree_properties():
+    g = G.rmat(10, 8, seed=311)
+    d = oracle.orient(g)
+    indeg = np.bincount(d.dag_col, minlength=g.n)
+    nid = oracle.reorder(g, oracle.REORDER_INDEGREE)
+    by_new = np.empty(g.n, dtype=np.int64)
+    by_new[nid] = np.arange(g.n)          # old id of each new id
+    seq = indeg[by_new]
+    assert np.all(seq[:-1] >= seq[1:])    # largest in-degree first
+    ties = seq[:-1] == seq[1:]
+    assert np.all(by_new[:-1][ties] < by_new[1:][ties])  # ties by old id
+
+
+def test_reorder_collective_properties():
+    g = G.rmat(10, 8, seed=312)
+    d = oracle.orient(g)
+    dp, dc = d.dag_ptr, d.dag_col
+    dplus = np.diff(dp)
+    coll = np.array([dplus[dc[dp[u]:dp[u + 1]]].sum() for u in range(g.n)])
+    top = int(np.lexsort((np.arange(g.n), -coll))[0])   # heaviest u, smallest id among ties
+    nid = oracle.reorder(g, oracle.REORDER_COLLECTIVE)
+    first = sorted(dc[dp[top]:dp[top + 1]].tolist())
+    # the heaviest vertex's out-neighbours receive the first ids, in id order
+    assert [int(nid[v]) for v in first] == list(range(len(first)))
+    # vertices in no out-list get the last ids, in id order
+    orphans = np.setdiff1d(np.arange(g.n), dc)
+    assert nid[orphans].tolist() == list(range(g.n - len(orphans), g.n))
+
+
+def test_collision_stats_against_algorithm1_tables():
+    # with levels >= d+ no bucket overflows, so Algorithm 1's tables hold the
+    # unbounded bucket loads and Eq. 2 from them must agree
+    g = G.rmat(9, 8, seed=93)
+    d = oracle.orient(g)
+    dp, dc = d.dag_ptr.tolist(), d.dag_col.tolist()
+    L = int(d.out_degrees().max())
+    mx, phi = oracle.collision_stats(d, "mod32")
+    assert phi == alg1.phi_eq2(dp, dc, 32, L)
+    assert mx == max(alg1.hash_table_construction(dc[dp[u]:dp[u + 1]], 32, L).max_collision()
+                     for u in range(g.n) if dp[u + 1] > dp[u])
+    # a multiplicative hash of 32 consecutive ids spreads them over all buckets
+    # (three-distance theorem: no bucket gets more than 2)
+    h = G.star(40)          # every leaf's out-list is {hub}; the hub's is empty
+    k = G.complete(34)      # N+(0) = {1..33}: consecutive ids
+    dk = oracle.orient(k)
+    assert oracle.collision_stats(dk, "mod32")[0] == 2          # 1 and 33 share bucket 1
+    assert oracle.collision_stats(dk, "mult32")[0] <= 2
+    assert oracle.collision_stats(oracle.orient(h), "mod32") == (1, 0)
