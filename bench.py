@@ -313,6 +313,29 @@ def measure_reorder(T, torch, dev, graphs):
     return rows
 
 
+def measure_ablation(T, torch, dev, graphs):
+    """Sec. 3.3 and Sec. 4.2 ablations on the given graphs: the worker cycles
+    spent building tables vs probing them (vertex-centric Algorithm 1 vs the
+    edge-centric Algorithm 2, which rebuilds N+(u)'s table for every
+    out-edge), and quad vs scalar 2-hop loads. Same counts in every mode."""
+    modes = [("vertex-centric, quad loads", {}), ("vertex-centric, scalar loads", dict(scalar_loads=1)),
+             ("edge-centric (Algorithm 2)", dict(edge_centric=1))]
+    rows = []
+    for name, (n, rp, col) in graphs.items():
+        base = None
+        for label, prm in modes:
+            with T.Context(dev.index, params=dict(prm, record_timing=2)) as c:
+                tri = c.count(n, rp, col)          # blocking: reads the cycle counters back
+                t = c.read_timing()
+                ms, tri2 = time_count(c, torch, dev, n, rp, col, reps=5)
+            base = tri if base is None else base
+            cyc = t["build_cycles"] + t["probe_cycles"]
+            rows.append({"graph": name, "mode": label, "count_ms": ms,
+                         "build_share": t["build_cycles"] / cyc if cyc else None,
+                         "count_equal": tri == base == tri2})
+    return rows
+
+
 # -------------------------------------------------------------- the arms
 
 def run_gb300(args):
@@ -454,6 +477,15 @@ def run_gb300(args):
               "rmat-s22-ef16-seed5": (big.n, torch.from_numpy(big.row_ptr.astype(np.int32)).to(dev),
                                       torch.from_numpy(np.ascontiguousarray(big.col, dtype=np.int32)).to(dev))}
         result["reorder_study"] = measure_reorder(T, torch, dev, gs)
+    if args.ablation:
+        import numpy as np
+
+        import graphgen as G
+        small = G.workload("rmat16")
+        gs = {WORKLOAD["name"]: (g.n, rp, col),
+              "rmat-s16-ef16-seed1": (small.n, torch.from_numpy(small.row_ptr.astype(np.int32)).to(dev),
+                                      torch.from_numpy(np.ascontiguousarray(small.col, dtype=np.int32)).to(dev))}
+        result["ablation_study"] = measure_ablation(T, torch, dev, gs)
     if not args.no_cpu_baseline:
         import oracle
         cores = oracle.max_threads()
@@ -506,6 +538,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", type=int, default=1, help="1: also time the 4096-graph batch (rank 0)")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--ablation", type=int, default=1,
+                    help="1: also run the build/probe split and edge-centric / load-width ablation (rank 0)")
     ap.add_argument("--reorder", type=int, default=1,
                     help="1: also run the Sec. 4.1 reordering study (rank 0)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,

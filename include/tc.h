@@ -96,9 +96,11 @@ typedef struct {
  * 6 levels cached in shared memory); a fuller bucket overflows to the next. */
 typedef struct {
     int32_t warp_max_out_degree; /* d+ above this -> thread-block worker, <= 255 (paper: 100; default 128) */
-    int32_t warp_area_ints;      /* shared-memory table area of one warp worker, ints (default 1088);
-                                    a warp-worker table has B = 2*nextpow2(d+) buckets of 4 slots */
-    int32_t warp_min_buckets;    /* fewest buckets of a warp-worker table, power of two >= 16 (default 16) */
+    int32_t warp_area_ints;      /* shared-memory table area of one warp worker, ints (default 1152);
+                                    a warp-worker table has 8*nextpow2(d+) slots in buckets of 2,
+                                    plus one length byte per bucket */
+    int32_t warp_min_buckets;    /* a warp-worker table has at least 4*warp_min_buckets slots; power of
+                                    two >= 16 (default 16) */
     int32_t block_threads;       /* threads of a thread-block worker (default 1024) */
     int32_t block_smem_bytes;    /* shared memory of a thread-block worker (default 200 KiB) */
     int32_t item_neighbors;      /* out-neighbours of a large vertex per work item, <= block_threads (default 1024) */
@@ -107,11 +109,16 @@ typedef struct {
     int32_t shard_count;         /* workload partition (Sec. 5.1): count only u with */
     int32_t shard_index;         /*   u % shard_count == shard_index (default 1 / 0) */
     int32_t validate;            /* reserved for extra input checks (0) */
-    int32_t record_timing;       /* 1: record CUDA events around the kernel phases (tc_read_timing) */
+    int32_t record_timing;       /* 1: record CUDA events around the kernel phases (tc_read_timing);
+                                    2: also count the workers' cycles in table builds and in probes
+                                    (blocking calls: tc_count, tc_count_dag, tc_count_host) */
     int32_t hash_mode;           /* 0: multiplicative hashing (default); 1: x mod B, Algorithm 1's hash */
     int32_t scalar_loads;        /* 0: warp workers read 2-hop lists as aligned 16-byte quads (default);
                                     1: one key per lane per load */
-    int32_t reserved[2];
+    int32_t edge_centric;        /* 1: ablation of Sec. 3.3's edge-centric design (Algorithm 2): the table
+                                    of N+(u) is rebuilt for every out-edge (u, v) and probed with N+(v);
+                                    slow by design, same counts (default 0) */
+    int32_t reserved[1];
 } tc_params;
 
 /* Per-DAG statistics (tc_dag_stats), all exact:
@@ -306,6 +313,10 @@ typedef struct {
     double orient_ms;  /* degree, keep counts, scan, compaction */
     double bin_ms;     /* out-degree binning */
     double count_ms;   /* hash build + probe + reduction (thread-block and warp workers) */
+    /* record_timing == 2: SM cycles the counting workers spent building tables
+     * and probing them, summed over warps (the split of Sec. 3.3's time-cost
+     * figure: hash table construction vs intersection) */
+    int64_t build_cycles, probe_cycles;
 } tc_timing;
 
 /* Wait for the recorded events, return the sums and start a new period. */

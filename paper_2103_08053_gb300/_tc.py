@@ -56,12 +56,12 @@ class tc_params(ctypes.Structure):
                 ("item_neighbors", c_int32), ("chunk", c_int32), ("warps_per_block", c_int32),
                 ("shard_count", c_int32), ("shard_index", c_int32), ("validate", c_int32),
                 ("record_timing", c_int32), ("hash_mode", c_int32), ("scalar_loads", c_int32),
-                ("reserved", c_int32 * 2)]
+                ("edge_centric", c_int32), ("reserved", c_int32 * 1)]
 
 
 class tc_timing(ctypes.Structure):
     _fields_ = [("calls", c_int64), ("orient_ms", ctypes.c_double), ("bin_ms", ctypes.c_double),
-                ("count_ms", ctypes.c_double)]
+                ("count_ms", ctypes.c_double), ("build_cycles", c_int64), ("probe_cycles", c_int64)]
 
 
 class tc_stats(ctypes.Structure):

@@ -91,7 +91,7 @@ DeviceGuard::~DeviceGuard() {
 static void fill_defaults(tc_params* p) {
     memset(p, 0, sizeof(*p));
     p->warp_max_out_degree = 128;
-    p->warp_area_ints = 1088;
+    p->warp_area_ints = pack_table_ints(128, 16);
     p->warp_min_buckets = 16;
     p->block_threads = 1024;
     p->block_smem_bytes = 200 * 1024;
@@ -127,6 +127,7 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         p.record_timing = in->record_timing;
         p.hash_mode = in->hash_mode;
         p.scalar_loads = in->scalar_loads;
+        p.edge_centric = in->edge_centric;
 #undef TAKE
     }
     if (p.warp_max_out_degree < 1 || p.warp_max_out_degree > 255)
@@ -151,6 +152,10 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
     if (p.hash_mode != 0 && p.hash_mode != 1) return ctx_fail(ctx, TC_ERR_INVALID_ARG, "hash_mode must be 0 or 1");
     if (p.scalar_loads != 0 && p.scalar_loads != 1)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "scalar_loads must be 0 or 1");
+    if (p.edge_centric != 0 && p.edge_centric != 1)
+        return ctx_fail(ctx, TC_ERR_INVALID_ARG, "edge_centric must be 0 or 1");
+    if (p.record_timing < 0 || p.record_timing > 2)
+        return ctx_fail(ctx, TC_ERR_INVALID_ARG, "record_timing must be 0, 1 or 2");
     if (p.chunk < 1 || p.chunk > 32) return ctx_fail(ctx, TC_ERR_INVALID_ARG, "chunk must be in [1, 32]");
     if (p.shard_count < 1 || p.shard_index < 0 || p.shard_index >= p.shard_count)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "need 0 <= shard_index < shard_count");
@@ -178,6 +183,8 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         cfg->record_timing = p.record_timing ? 1 : 0;
         cfg->hash_mode = p.hash_mode;
         cfg->quad_loads = p.scalar_loads ? 0 : 1;
+        cfg->cycle_timing = p.record_timing == 2 ? 1 : 0;
+        cfg->edge_centric = p.edge_centric;
         cfg->warp_grid = cfg->block_grid = 0;
     }
     return TC_OK;
@@ -286,6 +293,8 @@ static tc_status read_counters(tc_ctx* ctx, Workspace& ws, cudaStream_t st, DevC
     if (s) return s;
     *out = *ctx->host_ctr;
     if (out->err) return ctx_fail(ctx, err_bits_status(out->err), "%s", err_bits_text(out->err));
+    ctx->cyc_build += (long long)out->cyc_build;
+    ctx->cyc_probe += (long long)out->cyc_probe;
     return TC_OK;
 }
 
@@ -509,8 +518,13 @@ tc_status tc_count(tc_ctx* ctx, const tc_csr* g, uint64_t* count_host, void* str
     tc_status s = tc_count_async(ctx, g, d_count, d_err, stream);
     if (s) return s;
     cudaError_t e = cudaMemcpyAsync(ctx->host_ctr, ctx->out_scalars.p, 16, cudaMemcpyDeviceToHost, st);
+    DevCounters c{};
+    if (e == cudaSuccess && ctx->cfg.cycle_timing)  // the workers' build / probe cycles
+        e = cudaMemcpyAsync(&c, ctx->ws.ctr.p, sizeof(c), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if ((s = cuda_status(ctx, e, "reading the count"))) return s;
+    ctx->cyc_build += (long long)c.cyc_build;
+    ctx->cyc_probe += (long long)c.cyc_probe;
     uint64_t cnt;
     int32_t err;
     memcpy(&cnt, ctx->host_ctr, 8);
@@ -590,6 +604,9 @@ tc_status tc_read_timing(tc_ctx* ctx, tc_timing* out) {
     }
     ctx->timed.clear();
     if (s) return s;
+    t.build_cycles = ctx->cyc_build;
+    t.probe_cycles = ctx->cyc_probe;
+    ctx->cyc_build = ctx->cyc_probe = 0;
     *out = t;
     return TC_OK;
 }

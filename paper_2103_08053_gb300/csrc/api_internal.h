@@ -109,6 +109,7 @@ struct tc_ctx {
     std::vector<tcg::TimedCall> timed;      // recorded, not yet read
     std::vector<tcg::TimedCall> timed_free; // event sets to reuse
     long long cfg_version = 0;              // bumped by tc_set_params
+    long long cyc_build = 0, cyc_probe = 0; // worker cycles read back by blocking calls (record_timing 2)
     tcg::BatchRunner* batch = nullptr;
     tcg::ServeState* serve = nullptr;
 };

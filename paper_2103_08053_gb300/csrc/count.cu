@@ -135,7 +135,7 @@ __device__ __forceinline__ int bucket_of(int w, int lgB, unsigned mult = kHashMu
 // the next bucket. sm: shared array; tab/lenw: int offsets of the slots and
 // of the length words; B = 2^lgB. Lengths count claims (<= keys <= 255).
 // Returns 1 when the key did not fit its home bucket (the table overflowed).
-template <int HM>
+template <int HM, int SL = 4>
 __device__ __forceinline__ int insert_b4(int* sm, int tab, int lenw, int lgB, int w, unsigned mult) {
     const int mask = (1 << lgB) - 1;
     int h = bucket_of<HM>(w, lgB, mult);
@@ -143,8 +143,8 @@ __device__ __forceinline__ int insert_b4(int* sm, int tab, int lenw, int lgB, in
         const int sh = 8 * (h & 3);
         const unsigned old = atomicAdd(reinterpret_cast<unsigned*>(sm + lenw + (h >> 2)), 1u << sh);
         const int slot = (old >> sh) & 0xff;
-        if (slot < 4) {
-            sm[tab + 4 * h + slot] = w;
+        if (slot < SL) {
+            sm[tab + SL * h + slot] = w;
             return s > 0;
         }
         h = (h + 1) & mask;
@@ -170,13 +170,40 @@ __device__ __forceinline__ void insert_b4w(int* sm, int tab, int lenw, int lgB, 
 
 __device__ __forceinline__ int match4(const int4 q, int w) { return (q.x == w) | (q.y == w) | (q.z == w) | (q.w == w); }
 
+// A bucket of SL slots (4: one 16-byte load; 2: one 8-byte load). A warp's
+// shared loads are served in phases of 8 (16-byte) or 16 (8-byte) lanes, and
+// lanes of one phase that hit different buckets in the same banks conflict:
+// with random buckets, 8-byte buckets cost about two thirds of the shared
+// wavefronts of 16-byte buckets per probe.
+template <int SL>
+struct Bucket;
+template <>
+struct Bucket<4> {
+    int4 q;
+    __device__ __forceinline__ static Bucket at(const int* sm, int tab, int h) {
+        return {*reinterpret_cast<const int4*>(sm + tab + 4 * h)};
+    }
+    __device__ __forceinline__ int match(int w) const { return match4(q, w); }
+    __device__ __forceinline__ bool full() const { return q.w != EMPTY; }
+};
+template <>
+struct Bucket<2> {
+    int2 q;
+    __device__ __forceinline__ static Bucket at(const int* sm, int tab, int h) {
+        return {*reinterpret_cast<const int2*>(sm + tab + 2 * h)};
+    }
+    __device__ __forceinline__ int match(int w) const { return (q.x == w) | (q.y == w); }
+    __device__ __forceinline__ bool full() const { return q.y != EMPTY; }
+};
+
 // Algorithm 1 linearSearch continued past a full bucket h0 (slow path).
-__device__ __noinline__ int probe_b4_chain(const int* sm, int tab, int mask, int h0, int w) {
+template <int SL>
+__device__ __noinline__ int probe_chain(const int* sm, int tab, int mask, int h0, int w) {
     int h = (h0 + 1) & mask;
     for (int s = 0; s < mask; ++s) {
-        const int4 q = *reinterpret_cast<const int4*>(sm + tab + 4 * h);
-        const int hit = match4(q, w);
-        if (hit | (q.w == EMPTY)) return hit;
+        const Bucket<SL> b = Bucket<SL>::at(sm, tab, h);
+        const int hit = b.match(w);
+        if (hit | !b.full()) return hit;
         h = (h + 1) & mask;
     }
     return 0;
@@ -186,7 +213,7 @@ __device__ __noinline__ int probe_b4_chain(const int* sm, int tab, int mask, int
 // with log2 B = km[q] & 0xffff (pack slot km[q] >> 16). A probe is one
 // 16-byte load and four compares; only a lane whose bucket is full and did
 // not match walks the overflow chain. NOKEY lanes never match.
-template <bool SLOT_HITS, int HM>
+template <bool SLOT_HITS, int HM, int SL>
 __device__ __forceinline__ uint32_t probe4(const int (&key)[VC_UNROLL], const int (&kt)[VC_UNROLL],
                                            const int (&km)[VC_UNROLL], const int* sm, int* stage, unsigned mult) {
     uint32_t hits = 0;
@@ -194,11 +221,11 @@ __device__ __forceinline__ uint32_t probe4(const int (&key)[VC_UNROLL], const in
     for (int q = 0; q < VC_UNROLL; ++q) {
         const int lg = km[q] & 0xffff;
         const int h = bucket_of<HM>(key[q], lg, mult);
-        const int4 b4 = *reinterpret_cast<const int4*>(sm + kt[q] + 4 * h);
-        int hit = match4(b4, key[q]);
-        const bool more = key[q] >= 0 && !hit && b4.w != EMPTY;
+        const Bucket<SL> b = Bucket<SL>::at(sm, kt[q], h);
+        int hit = b.match(key[q]);
+        const bool more = key[q] >= 0 && !hit && b.full();
         if (__any_sync(FULL, more)) {
-            if (more) hit = probe_b4_chain(sm, kt[q], (1 << lg) - 1, h, key[q]);
+            if (more) hit = probe_chain<SL>(sm, kt[q], (1 << lg) - 1, h, key[q]);
         }
         hits += hit;
         if (SLOT_HITS && hit) atomicAdd(&stage[128 + (km[q] >> 16)], 1);
@@ -215,7 +242,7 @@ __device__ __forceinline__ uint32_t probe4(const int (&key)[VC_UNROLL], const in
 // before its probes. A probe is one 16-byte load and four compares; only a
 // lane whose bucket is full and did not match walks the overflow chain.
 // Returns the hits; *done = number of combined indices processed.
-template <bool SLOT_HITS, int HM>
+template <bool SLOT_HITS, int HM, int SL = 4>
 __device__ __forceinline__ uint32_t vc_range_b4(int s, int l, int tab, int lgB, int slot, int skip, int limit,
                                                 const int* sm, const int32_t* __restrict__ dag_col, int lane,
                                                 int* stage, int* done, unsigned mult = kHashMult0) {
@@ -258,7 +285,7 @@ __device__ __forceinline__ uint32_t vc_range_b4(int s, int l, int tab, int lgB, 
             const int f = b + lane;
             key[q] = (f < end) ? __ldg(dag_col + bo + f) : NOKEY;
         }
-        hits += probe4<SLOT_HITS, HM>(key, kt, km, sm, stage, mult);
+        hits += probe4<SLOT_HITS, HM, SL>(key, kt, km, sm, stage, mult);
     }
     *done = end > skip ? end - skip : 0;
     return hits;
@@ -273,7 +300,7 @@ __device__ __forceinline__ uint32_t vc_range_b4(int s, int l, int tab, int lgB, 
 // starts <= f) - 1, one shared load and two popcounts per window; longer
 // chunks use vc_owner.
 constexpr int BITMAP_WORDS = 64;  // 2048 combined indices
-template <bool SLOT_HITS, int HM>
+template <bool SLOT_HITS, int HM, int SL>
 __device__ __forceinline__ uint32_t vc_pack_fast(int s, int l, int td, const int* sm,
                                                  const int32_t* __restrict__ dag_col, int lane, int* stage,
                                                  unsigned mult) {
@@ -331,8 +358,7 @@ __device__ __forceinline__ uint32_t vc_pack_fast(int s, int l, int td, const int
 #pragma unroll
         for (int q = 0; q < VC_UNROLL; ++q) {
             const int h = bucket_of<HM>(key[q], (kd[q] >> 16) & 31, mult);
-            const int4 b4 = *reinterpret_cast<const int4*>(sm + (kd[q] & 0xffff) + 4 * h);
-            const int hit = match4(b4, key[q]);
+            const int hit = Bucket<SL>::at(sm, kd[q] & 0xffff, h).match(key[q]);
             hits += hit;
             if (SLOT_HITS && hit) atomicAdd(&stage[128 + ((kd[q] >> 21) & 31)], 1);
         }
@@ -352,7 +378,7 @@ __device__ __forceinline__ uint32_t vc_pack_fast(int s, int l, int td, const int
 // starts in quad space when the lists span <= BITMAP_WORDS * 32 quads, else
 // vc_owner.
 constexpr int QUAD_UNROLL = 2;  // quads in flight per lane
-template <bool SLOT_HITS, int HM>
+template <bool SLOT_HITS, int HM, int SL>
 __device__ __forceinline__ uint32_t vc_pack_quad(int s, int l, int td, const int* sm,
                                                  const int32_t* __restrict__ dag_col, int m, int lane, int* stage,
                                                  unsigned mult) {
@@ -437,8 +463,7 @@ __device__ __forceinline__ uint32_t vc_pack_quad(int s, int l, int td, const int
             for (int j = 0; j < 4; ++j) {
                 if (j >= lo[q] && j < hi[q]) {
                     const int h = bucket_of<HM>(key[j], lg, mult);
-                    const int4 b4 = *reinterpret_cast<const int4*>(sm + tab + 4 * h);
-                    hq += match4(b4, key[j]);
+                    hq += Bucket<SL>::at(sm, tab, h).match(key[j]);
                 }
             }
             hits += hq;
@@ -528,7 +553,7 @@ __device__ __forceinline__ uint32_t vc_range_quad(int s, int e, int nq, int tab,
             }
             if (__any_sync(FULL, more)) {
                 for (int j = 0; j < 4; ++j)
-                    if ((more >> j) & 1) hits += probe_b4_chain(sm, tab, mask, bucket_of<HM>(key[j], lgB), key[j]);
+                    if ((more >> j) & 1) hits += probe_chain<4>(sm, tab, mask, bucket_of<HM>(key[j], lgB), key[j]);
             }
         }
     }
@@ -581,11 +606,12 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
     k_count_pack(const int32_t* __restrict__ dag_ptr, const int32_t* __restrict__ dag_col,
                  const int2* __restrict__ desc, const int32_t* __restrict__ warp_list,
                  unsigned long long* __restrict__ per_vertex, DevCounters* ctr, int n, int area_ints,
-                 int lg_min_buckets, int pop, int quad) {
+                 int lg_min_buckets, int pop, int quad, int timing) {
     extern __shared__ int smem[];
     if (ctr->err) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int m = quad ? __ldg(dag_ptr + n) : 0;  // readable dag_col entries (quad path)
+    long long cyc_b = 0, cyc_p = 0;               // build / probe cycles (timing only)
     const unsigned le = lanemask_le(lane);
     const int area = w * (area_ints + STAGE_INTS);  // int offset of this warp's area in smem
     int* stage = smem + area + area_ints;
@@ -603,10 +629,11 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
             a = d.x;
             k = d.y;
         }
+        // 8 * nextpow2(k) slots (at least 4 * min_buckets) in buckets of PACK_SLOTS
         int lgB = 33 - __clz(k > 1 ? k - 1 : 1);  // log2(2 * nextpow2(k))
-        lgB = lgB < lg_min_buckets ? lg_min_buckets : lgB;
+        lgB = (lgB < lg_min_buckets ? lg_min_buckets : lgB) + (PACK_SLOTS == 2 ? 1 : 0);
         const int B = 1 << lgB;
-        const int ftab = (lane < cnt) ? 4 * B : 0, flen = (lane < cnt) ? B / 4 : 0;
+        const int ftab = (lane < cnt) ? PACK_SLOTS * B : 0, flen = (lane < cnt) ? B / 4 : 0;
         for (int p0 = 0; p0 < cnt;) {
             // the pack: the longest run of vertices from p0 whose tables fit the area
             const int ft = lane >= p0 ? ftab : 0, fl = lane >= p0 ? flen : 0;
@@ -626,6 +653,7 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
             const int Kex = K - kk;
             const int kbias = a - Kex;  // dag_col index of flat out-edge e owned by this lane
             const int E = __shfl_sync(FULL, K, 31);
+            const long long t_build = timing ? clock64() : 0;
             unsigned mult = kHashMult0;
             bool chained = false;
             for (int attempt = 0;; ++attempt) {
@@ -650,7 +678,7 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
                         const int tb = __shfl_sync(FULL, my_tab, own[q]);
                         const int lw = __shfl_sync(FULL, my_len, own[q]);
                         const int lg = __shfl_sync(FULL, lgB, own[q]);
-                        if (key[q] >= 0) ovf |= insert_b4<HM>(smem, tb, lw, lg, key[q], mult);
+                        if (key[q] >= 0) ovf |= insert_b4<HM, PACK_SLOTS>(smem, tb, lw, lg, key[q], mult);
                     }
                 }
                 __syncwarp();
@@ -661,6 +689,8 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
                 }
                 mult = hash_mult(attempt + 1);
             }
+            const long long t_probe = timing ? clock64() : 0;
+            if (timing) cyc_b += t_probe - t_build;
             // probe: chunks of 32 out-edges, bounds of the next chunk prefetched
             uint32_t hits = 0;
             int s = 0, l = 0, etab = 0, elg = 0, eslot = 0;
@@ -684,14 +714,14 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
                     list_bounds(e < E ? __ldg(dag_col + bo + e) : -1, dag_ptr, n, ctr, ns, nl);
                 }
                 if (!chained && quad) {
-                    hits += vc_pack_quad<PER_VERTEX, HM>(s, l, etab | (elg << 16) | (eslot << 21), smem, dag_col,
+                    hits += vc_pack_quad<PER_VERTEX, HM, PACK_SLOTS>(s, l, etab | (elg << 16) | (eslot << 21), smem, dag_col,
                                                          m, lane, stage, mult);
                 } else if (!chained) {
-                    hits += vc_pack_fast<PER_VERTEX, HM>(s, l, etab | (elg << 16) | (eslot << 21), smem, dag_col,
+                    hits += vc_pack_fast<PER_VERTEX, HM, PACK_SLOTS>(s, l, etab | (elg << 16) | (eslot << 21), smem, dag_col,
                                                          lane, stage, mult);
                 } else {
                     int done;
-                    hits += vc_range_b4<PER_VERTEX, HM>(s, l, etab, elg, eslot, 0, 0x7fffffff, smem, dag_col, lane,
+                    hits += vc_range_b4<PER_VERTEX, HM, PACK_SLOTS>(s, l, etab, elg, eslot, 0, 0x7fffffff, smem, dag_col, lane,
                                                         stage, &done, mult);
                 }
                 s = ns;
@@ -701,6 +731,7 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
                 eslot = nslot;
             }
             acc += hits;
+            if (timing) cyc_p += clock64() - t_probe;
             if (PER_VERTEX) {
                 __syncwarp();
                 if (in) per_vertex[__ldg(warp_list + i0 + lane)] = (unsigned long long)stage[128 + lane];
@@ -708,6 +739,10 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
             __syncwarp();
             p0 = p1;
         }
+    }
+    if (timing && lane == 0) {
+        atomicAdd(&ctr->cyc_build, (unsigned long long)cyc_b);
+        atomicAdd(&ctr->cyc_probe, (unsigned long long)cyc_p);
     }
     block_add_total(acc, ctr);
 }
@@ -725,11 +760,12 @@ template <int PIECE, int HM>
 __global__ void __launch_bounds__(1024, 1)
     k_count_block(const int32_t* __restrict__ dag_ptr, const int32_t* __restrict__ dag_col,
                   const int2* __restrict__ items, unsigned long long* __restrict__ per_vertex, DevCounters* ctr,
-                  int n, int table_off, int part_max, int item_nbrs, int quad) {
+                  int n, int table_off, int part_max, int item_nbrs, int quad, int timing) {
     extern __shared__ int smem[];
     __shared__ int s_item, s_piece;
     __shared__ int s_wsum[32];
     if (ctr->err) return;
+    long long cyc_b = 0, cyc_p = 0;  // build / probe cycles of this warp (timing only)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int m = quad ? __ldg(dag_ptr + n) : 0;  // readable dag_col entries (quad path)
     int* stage = smem + w * BLOCK_STAGE_INTS;
@@ -774,6 +810,7 @@ __global__ void __launch_bounds__(1024, 1)
             const int pk = min(part_max, k - p0);
             const int B = next_pow2(pk < 32 ? 32 : pk);
             const int lgB = 31 - __clz(B);
+            const long long t_build = timing ? clock64() : 0;
             int* tab = smem + table_off;
             const int lenw = table_off + 4 * B;
             for (int t = threadIdx.x * 4; t < 4 * B; t += blockDim.x * 4)
@@ -784,6 +821,8 @@ __global__ void __launch_bounds__(1024, 1)
             for (int t = threadIdx.x; t < pk; t += blockDim.x)
                 insert_b4w<HM>(smem, table_off, lenw, lgB, __ldg(dag_col + a + p0 + t));
             __syncthreads();
+            const long long t_probe = timing ? clock64() : 0;
+            if (timing) cyc_b += t_probe - t_build;
             const int piece = quad ? PIECE / 4 : PIECE;  // combined units (quads or keys) per piece
             for (;;) {
                 int pc = 0;
@@ -815,12 +854,90 @@ __global__ void __launch_bounds__(1024, 1)
                 }
             }
             __syncthreads();
+            if (timing) cyc_p += clock64() - t_probe;
         }
         acc += h;
         if (per_vertex) {
             const unsigned long long hu = warp_sum_u64(h);
             if (lane == 0 && hu) atomicAdd(&per_vertex[u], hu);
         }
+    }
+    if (timing && lane == 0) {
+        atomicAdd(&ctr->cyc_build, (unsigned long long)cyc_b);
+        atomicAdd(&ctr->cyc_probe, (unsigned long long)cyc_p);
+    }
+    block_add_total(acc, ctr);
+}
+
+// Ablation of the edge-centric design (Sec. 3.3, Algorithm 2): a warp takes
+// a vertex u and, for every out-edge (u, v), builds the table of N+(u) afresh
+// and probes it with N+(v) -- the table is rebuilt d+(u) times instead of
+// once. Out-lists longer than the warp's area holds are built part by part,
+// each part probed with all of N+(v). Tables are the pack tables' bucket-of-4
+// layout with overflow chains; keys are read one per lane.
+template <int HM>
+__global__ void __launch_bounds__(256) k_count_edge(const int32_t* __restrict__ dag_ptr,
+                                                   const int32_t* __restrict__ dag_col,
+                                                   unsigned long long* __restrict__ per_vertex, DevCounters* ctr,
+                                                   int n, int area_ints, int part_max, int shard_count,
+                                                   int shard_index, int timing) {
+    extern __shared__ int smem[];
+    if (ctr->err) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int area = w * (area_ints + STAGE_INTS);
+    long long cyc_b = 0, cyc_p = 0;
+    unsigned long long acc = 0;
+    for (;;) {
+        int u = 0;
+        if (lane == 0) u = atomicAdd(&ctr->q_warp, 1);
+        u = __shfl_sync(FULL, u, 0);
+        if (u >= n) break;
+        if (shard_count > 1 && u % shard_count != shard_index) continue;
+        const int a = dag_ptr[u], k = dag_ptr[u + 1] - a;
+        if (k < 2) continue;
+        uint32_t hu = 0;
+        for (int e = 0; e < k; ++e) {
+            int s = 0, l = 0;
+            list_bounds(__ldg(dag_col + a + e), dag_ptr, n, ctr, s, l);
+            for (int p0 = 0; p0 < k; p0 += part_max) {
+                const long long t0 = timing ? clock64() : 0;
+                const int pk = min(part_max, k - p0);
+                int lgB = 33 - __clz(pk > 1 ? pk - 1 : 1);
+                lgB = lgB < 4 ? 4 : lgB;
+                const int B = 1 << lgB;
+                const int tab = area, lenw = area + 4 * B;
+                for (int t = lane * 4; t < 4 * B; t += 128)
+                    *reinterpret_cast<int4*>(smem + tab + t) = make_int4(EMPTY, EMPTY, EMPTY, EMPTY);
+                for (int t = lane; t < B / 4; t += 32) smem[lenw + t] = 0;
+                __syncwarp();
+                for (int t = lane; t < pk; t += 32) insert_b4<HM>(smem, tab, lenw, lgB, __ldg(dag_col + a + p0 + t),
+                                                                 kHashMult0);
+                __syncwarp();
+                const long long t1 = timing ? clock64() : 0;
+                for (int i = lane; i < l; i += 32) {
+                    const int key = __ldg(dag_col + s + i);
+                    const int h = bucket_of<HM>(key, lgB);
+                    const int4 b4 = *reinterpret_cast<const int4*>(smem + tab + 4 * h);
+                    int hit = match4(b4, key);
+                    if (!hit && b4.w != EMPTY) hit = probe_chain<4>(smem, tab, B - 1, h, key);
+                    hu += hit;
+                }
+                __syncwarp();
+                if (timing) {
+                    cyc_b += t1 - t0;
+                    cyc_p += clock64() - t1;
+                }
+            }
+        }
+        acc += hu;
+        if (per_vertex) {
+            const unsigned long long t = warp_sum_u64(hu);
+            if (lane == 0 && t) atomicAdd(&per_vertex[u], t);
+        }
+    }
+    if (timing && lane == 0) {
+        atomicAdd(&ctr->cyc_build, (unsigned long long)cyc_b);
+        atomicAdd(&ctr->cyc_probe, (unsigned long long)cyc_p);
     }
     block_add_total(acc, ctr);
 }
@@ -924,7 +1041,7 @@ __global__ void __launch_bounds__(256) k_collision(const int32_t* __restrict__ d
 int pack_smem_bytes(const CountCfg& cfg) { return cfg.warps_per_block * (cfg.warp_area_ints + STAGE_INTS) * 4; }
 
 using PackKernel = void (*)(const int32_t*, const int32_t*, const int2*, const int32_t*, unsigned long long*,
-                            DevCounters*, int, int, int, int, int);
+                            DevCounters*, int, int, int, int, int, int);
 
 PackKernel pack_kernel(bool per_vertex, int hm) {
     if (hm == 1) return per_vertex ? k_count_pack<true, 1> : k_count_pack<false, 1>;
@@ -932,9 +1049,27 @@ PackKernel pack_kernel(bool per_vertex, int hm) {
 }
 
 using BlockKernel = void (*)(const int32_t*, const int32_t*, const int2*, unsigned long long*, DevCounters*, int,
-                             int, int, int, int);
+                             int, int, int, int, int);
 
 BlockKernel block_kernel(int hm) { return hm == 1 ? k_count_block<BLOCK_PIECE, 1> : k_count_block<BLOCK_PIECE, 0>; }
+
+using EdgeKernel = void (*)(const int32_t*, const int32_t*, unsigned long long*, DevCounters*, int, int, int, int,
+                            int, int);
+
+EdgeKernel edge_kernel(int hm) { return hm == 1 ? k_count_edge<1> : k_count_edge<0>; }
+
+// Largest part of N+(u) whose pack table (B = 2 * nextpow2(part) >= 16
+// buckets, 4B slots + B/4 byte-length words) fits a warp's area.
+int edge_part_max(int area_ints) {
+    int p = 1;
+    while (true) {
+        int b = 2 * next_pow2(2 * p);
+        if (b < 16) b = 16;
+        if (4 * b + b / 4 > area_ints) break;
+        p *= 2;
+    }
+    return p;
+}
 
 int lg2(int x) {
     int l = 0;
@@ -947,7 +1082,8 @@ int lg2(int x) {
 int pack_table_ints(int max_out_degree, int min_buckets) {
     int b = 2 * next_pow2(max_out_degree < 1 ? 1 : max_out_degree);
     if (b < min_buckets) b = min_buckets;
-    return 4 * b + b / 4;
+    const int slots = 4 * b, buckets = slots / PACK_SLOTS;
+    return slots + buckets / 4;  // slots, byte lengths
 }
 
 // Shared-memory ints a thread-block worker has for its table, after the
@@ -975,6 +1111,8 @@ cudaError_t count_kernel_setup(CountCfg& cfg, int num_sms) {
     e = cudaFuncSetAttribute(block_kernel(cfg.hash_mode), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              cfg.block_smem_bytes);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(edge_kernel(cfg.hash_mode), cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem);
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pack_kernel(false, cfg.hash_mode),
                                                       cfg.warps_per_block * 32,
@@ -991,16 +1129,23 @@ cudaError_t count_kernel_setup(CountCfg& cfg, int num_sms) {
 cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t n, const int32_t* warp_list,
                          const int2* warp_desc, const int2* items, unsigned long long* per_vertex,
                          const CountCfg& cfg, DevCounters* ctr, cudaStream_t st, long long* launches) {
+    if (cfg.edge_centric) {
+        *launches += 1;
+        edge_kernel(cfg.hash_mode)<<<cfg.warp_grid, cfg.warps_per_block * 32, pack_smem_bytes(cfg), st>>>(
+            dag_ptr, dag_col, per_vertex, ctr, (int)n, cfg.warp_area_ints, edge_part_max(cfg.warp_area_ints),
+            cfg.shard_count, cfg.shard_index, cfg.cycle_timing);
+        return cudaGetLastError();
+    }
     *launches += 2;
     const int table_off = (cfg.block_threads / 32) * BLOCK_STAGE_INTS + 3 * cfg.item_neighbors;
     const int quad = (cfg.quad_loads && ((uintptr_t)dag_col & 15) == 0) ? 1 : 0;
     block_kernel(cfg.hash_mode)<<<cfg.block_grid, cfg.block_threads, cfg.block_smem_bytes, st>>>(
         dag_ptr, dag_col, items, per_vertex, ctr, (int)n, table_off, count_block_part_max(cfg), cfg.item_neighbors,
-        quad);
+        quad, cfg.cycle_timing);
     pack_kernel(per_vertex != nullptr, cfg.hash_mode)<<<cfg.warp_grid, cfg.warps_per_block * 32,
                                                       pack_smem_bytes(cfg), st>>>(
         dag_ptr, dag_col, warp_desc, warp_list, per_vertex, ctr, (int)n, cfg.warp_area_ints,
-        lg2(cfg.warp_min_buckets), cfg.chunk, quad);
+        lg2(cfg.warp_min_buckets), cfg.chunk, quad, cfg.cycle_timing);
     return cudaGetLastError();
 }
 

@@ -6,6 +6,11 @@
 
 #include "tc.h"
 
+// Slots per bucket of the warp workers' (pack) tables: 2 (8-byte buckets) or 4.
+#ifndef PACK_SLOTS
+#define PACK_SLOTS 2
+#endif
+
 namespace tcg {
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -22,6 +27,7 @@ enum : int {
 struct DevCounters {
     unsigned long long total;  // triangle count
     long long m;               // DAG edges (scan total)
+    unsigned long long cyc_build, cyc_probe;  // worker cycles in table builds / probes (cycle timing only)
     int n_warp;                // vertices in the warp-worker list
     int n_items;               // work items of thread-block workers
     int n_block;               // vertices with d+ > warp threshold
@@ -30,9 +36,9 @@ struct DevCounters {
     int err;                   // ERRBIT_* flags
     int n_hub;                 // rows with degree > HUB_DEGREE (orientation by thread blocks)
     int q_hub[2];              // hub-row cursors of the two orientation passes
-    int pad[3];
+    int pad[14];
 };
-static_assert(sizeof(DevCounters) == 64, "DevCounters layout");
+static_assert(sizeof(DevCounters) == 128, "DevCounters layout");
 
 // Resolved launch parameters (host fills from tc_params + device properties).
 struct CountCfg {
@@ -50,6 +56,8 @@ struct CountCfg {
     int record_timing;
     int hash_mode;  // 0 multiplicative, 1 x mod B
     int quad_loads; // 1: warp workers read 2-hop lists as 16-byte quads (when dag_col is 16-byte aligned)
+    int cycle_timing;  // 1: counting kernels add their build / probe cycles to DevCounters
+    int edge_centric;  // 1: Algorithm 2 ablation (table of N+(u) rebuilt for every out-edge)
 };
 
 // One graph of an orientation pass. A batch places its graphs in one padded

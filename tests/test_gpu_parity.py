@@ -192,17 +192,19 @@ def T_tc():
 
 PARAM_SETS = {
     "tiny_block_items": dict(warp_max_out_degree=8, item_neighbors=32),  # many block items per vertex
-    "one_table_per_pack": dict(warp_max_out_degree=12, warp_area_ints=136),
+    "one_table_per_pack": dict(warp_max_out_degree=12, warp_area_ints=144),
     "all_block": dict(warp_max_out_degree=1),                  # every vertex on the block path
-    "all_warp": dict(warp_max_out_degree=255, warp_area_ints=2176, warps_per_block=4),
+    "all_warp": dict(warp_max_out_degree=255, warp_area_ints=2304, warps_per_block=4),
     "one_per_pop": dict(chunk=1),
-    "big_min_buckets": dict(warp_min_buckets=512, warp_area_ints=2176),
+    "big_min_buckets": dict(warp_min_buckets=512, warp_area_ints=2304),
     "small_items": dict(item_neighbors=32, warp_max_out_degree=16),
     "split_parts": dict(block_threads=64, block_smem_bytes=8192, item_neighbors=64, warp_max_out_degree=8),
     # ^ part_max = 256: out-lists longer than 256 are probed part by part
     "chunk7": dict(chunk=7, warp_area_ints=4608),
     "paper_hash": dict(hash_mode=1),
     "scalar_loads": dict(scalar_loads=1),                      # one 2-hop key per lane per load
+    "edge_centric": dict(edge_centric=1),                      # Algorithm 2 ablation: a table per out-edge
+    "cycle_timing": dict(record_timing=2),
 }
 
 
@@ -223,7 +225,7 @@ def _bucket_collision_graph(k, stride=1024):
     return G.from_edge_list(n, e)
 
 
-@pytest.mark.parametrize("k,params", [(60, {}), (300, {}), (200, dict(warp_max_out_degree=255, warp_area_ints=2176)),
+@pytest.mark.parametrize("k,params", [(60, {}), (300, {}), (200, dict(warp_max_out_degree=255, warp_area_ints=2304)),
                                       (600, {}), (500, dict(block_threads=64, block_smem_bytes=8192,
                                                              item_neighbors=64))])
 @pytest.mark.parametrize("hash_mode", [1, 0])
@@ -332,3 +334,19 @@ def test_phase_timing_and_launch_count(T):
         t = c.read_timing()
         assert t["calls"] == 1 and t["orient_ms"] > 0 and t["count_ms"] > 0
         assert c.read_timing()["calls"] == 0
+
+
+def test_build_probe_cycle_split(T):
+    # record_timing = 2: the workers' cycles in table builds and in probes. The
+    # edge-centric ablation rebuilds N+(u)'s table once per out-edge, so its
+    # build share must exceed the vertex-centric one (Sec. 3.3).
+    g = G.rmat(14, 16, seed=23)
+    shares = {}
+    for ec in (0, 1):
+        with T.Context(0, params=dict(record_timing=2, edge_centric=ec)) as c:
+            assert gpu_count(c, g) == oracle.count(g)
+            t = c.read_timing()
+            assert t["build_cycles"] > 0 and t["probe_cycles"] > 0
+            shares[ec] = t["build_cycles"] / (t["build_cycles"] + t["probe_cycles"])
+            assert c.read_timing()["build_cycles"] == 0      # reading starts a new period
+    assert shares[1] > shares[0]
