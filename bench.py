@@ -34,6 +34,12 @@ if ROOT not in sys.path:
 
 WORKLOAD = dict(name="rgg-2^22-meandeg64-seed2", points_log2=22, mean_degree=64.0, seed=2)
 REF_SAMPLE = dict(name="rgg-2^20-meandeg64-seed2", points_log2=20, mean_degree=64.0, seed=2)
+# --workload: the other single-graph configurations, measured the same way
+OTHER_WORKLOADS = {
+    "rmat16": dict(name="rmat-s16-ef16-seed1", graph="rmat16"),
+    "rmat22": dict(name="rmat-s22-ef16-seed1", graph="rmat22"),
+    "rmat26": dict(name="rmat-s26-ef16-seed3", graph="rmat26"),
+}
 METRIC = "triangle-count TEPS"
 UNIT = "edges/s"
 FALLBACK_HBM_GBS = 6800.0
@@ -51,6 +57,8 @@ def dist_env():
 
 def make_graph(spec):
     import graphgen as G
+    if "graph" in spec:
+        return G.workload(spec["graph"])
     return G.rgg(1 << spec["points_log2"], spec["mean_degree"], seed=spec["seed"])
 
 
@@ -434,7 +442,7 @@ def run_gb300(args):
     count_ms = tm["count_ms"] / max(tm["calls"], 1)
     bytes_count = count_phase_bytes(g.n, g.m, st["wedges_plus"])
     achieved = bytes_count / (count_ms / 1e3) / 1e9
-    traffic = profiled_traffic()
+    traffic = profiled_traffic() if WORKLOAD["name"] == "rgg-2^22-meandeg64-seed2" else None
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -538,6 +546,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", type=int, default=1, help="1: also time the 4096-graph batch (rank 0)")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--workload", choices=["rgg22", *OTHER_WORKLOADS], default="rgg22",
+                    help="graph of the timed steps (default: the RGG 2^22 benchmark graph); the batched, serving "
+                         "and study sections always use their own workloads")
     ap.add_argument("--ablation", type=int, default=1,
                     help="1: also run the build/probe split and edge-centric / load-width ablation (rank 0)")
     ap.add_argument("--reorder", type=int, default=1,
@@ -547,6 +558,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.workload != "rgg22":
+        global WORKLOAD
+        WORKLOAD = OTHER_WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -221,6 +221,7 @@ tc_status tcg::ensure_orient_ws(tc_ctx* ctx, Workspace& ws, int64_t n, int64_t n
     if ((s = ws.kept.ensure(ctx, (size_t)(n + 1) * 4, st))) return s;
     if ((s = ws.partial.ensure(ctx, (size_t)(scan_blocks(n) + 2) * 8, st))) return s;
     if ((s = ws.hubs.ensure(ctx, (size_t)(n + 1) * 4, st))) return s;
+    if ((s = ws.kbits.ensure(ctx, (size_t)keep_bits_words(nnz) * 4, st))) return s;
     return ensure_count_ws(ctx, ws, n, nnz / 2, st);
 }
 
@@ -256,7 +257,7 @@ static tc_status enqueue_orient(tc_ctx* ctx, Workspace& ws, const tc_csr* g, int
     long long nl = 0;
     cudaError_t e = launch_orient(g->row_ptr, g->offset_bits, g->col, g->n, g->nnz, (int32_t*)ws.deg.p,
                                   (int32_t*)ws.kept.p, (long long*)ws.partial.p, dag_ptr, dag_col, cap,
-                                  (int32_t*)ws.hubs.p, ctr, ctx->num_sms, st, &nl);
+                                  (int32_t*)ws.hubs.p, (unsigned*)ws.kbits.p, ctr, ctx->num_sms, st, &nl);
     ctx->launches += nl;
     if (g->n == 0 && e == cudaSuccess) e = cudaMemsetAsync(dag_ptr, 0, sizeof(int32_t), st);
     return cuda_status(ctx, e, "orientation kernels");

@@ -77,7 +77,7 @@ template <typename Off, bool COMPACT, bool BATCH>
 __global__ void __launch_bounds__(ORIENT_THREADS)
     k_orient(GraphRef one, const GraphRef* __restrict__ gs, int k, int64_t total, const int32_t* __restrict__ deg,
              int32_t* __restrict__ kept, const int32_t* __restrict__ dag_ptr, int32_t* __restrict__ dag_col,
-             int64_t dag_cap, DevCounters* ctr) {
+             int64_t dag_cap, unsigned* __restrict__ kbits, DevCounters* ctr) {
     __shared__ long long s_st[ORIENT_WARPS][33];
     __shared__ long long s_as[ORIENT_WARPS][32];
     __shared__ int s_cnt[ORIENT_WARPS][32];
@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
             // issue every load of the step first: ORIENT_UNROLL col reads, then
             // their degree gathers, so each lane has that many requests in flight
             int vq[ORIENT_UNROLL], dq[ORIENT_UNROLL];
+            long long atq[ORIENT_UNROLL];
 #pragma unroll
             for (int q = 0; q < ORIENT_UNROLL; ++q) {
                 const long long f = base + 32 * q + lane;
@@ -145,11 +146,15 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
                     while (st[rq + 1] <= f) ++rq;
                     at = as[rq] + (f - st[rq]);
                 }
+                atq[q] = at;
                 vq[q] = (f < ge) ? __ldg(col + at) : -1;
             }
+            // the compaction pass reads the count pass's keep bits instead of
+            // gathering the neighbours' degrees again
+            const bool gather = !(COMPACT && kbits);
 #pragma unroll
             for (int q = 0; q < ORIENT_UNROLL; ++q)
-                dq[q] = ((unsigned)vq[q] < (unsigned long long)n) ? __ldg(deg + vb + vq[q]) : 0;
+                dq[q] = (gather && (unsigned)vq[q] < (unsigned long long)n) ? __ldg(deg + vb + vq[q]) : 0;
 #pragma unroll
             for (int q = 0; q < ORIENT_UNROLL; ++q) {
                 const long long f = base + 32 * q + lane;
@@ -158,7 +163,9 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
                 const int v = vq[q];
                 if (act) {
                     while (st[r + 1] <= f) ++r;
-                    if ((unsigned)v >= (unsigned long long)n) {
+                    if (!gather) {
+                        keep = (__ldg(kbits + (atq[q] >> 5)) >> (atq[q] & 31)) & 1u;
+                    } else if ((unsigned)v >= (unsigned long long)n) {
                         atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
                     } else {
                         const int du = (int)(st[r + 1] - st[r]);  // rows in the walk are not hubs
@@ -169,6 +176,21 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
                 const unsigned km = __ballot_sync(FULL, keep);
                 const unsigned am = __ballot_sync(FULL, act);
                 if (am == 0) break;
+                if (!COMPACT && kbits) {
+                    // keep bit of entry `at` -> kbits; a hubless walk covers 32
+                    // consecutive entries, whose bits lane 0 writes as one word
+                    // split over the two words it straddles
+                    if (hubless) {
+                        if (lane == 0 && km) {
+                            const long long a0 = atq[q];
+                            const int sh = (int)(a0 & 31);
+                            atomicOr(kbits + (a0 >> 5), km << sh);
+                            if (sh) atomicOr(kbits + (a0 >> 5) + 1, km >> (32 - sh));
+                        }
+                    } else if (keep) {
+                        atomicOr(kbits + (atq[q] >> 5), 1u << (atq[q] & 31));
+                    }
+                }
                 const int rp = __shfl_up_sync(FULL, r, 1);
                 const int rn = __shfl_down_sync(FULL, r, 1);
                 const bool seg_start = act && (lane == 0 || rp != r);
@@ -212,7 +234,7 @@ template <typename Off, bool COMPACT, bool BATCH>
 __global__ void __launch_bounds__(HUB_THREADS)
     k_orient_hub(GraphRef one, const GraphRef* __restrict__ gs, int k, const int32_t* __restrict__ hubs,
                  const int32_t* __restrict__ deg, int32_t* __restrict__ kept, const int32_t* __restrict__ dag_ptr,
-                 int32_t* __restrict__ dag_col, int64_t dag_cap, DevCounters* ctr) {
+                 int32_t* __restrict__ dag_col, int64_t dag_cap, unsigned* __restrict__ kbits, DevCounters* ctr) {
     __shared__ int s_row, s_carry;
     __shared__ int s_w[HUB_THREADS / 32];
     if (COMPACT && ctr->err) return;
@@ -239,11 +261,14 @@ __global__ void __launch_bounds__(HUB_THREADS)
             bool kq[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) v[q] = (e0 + q < b) ? __ldg(G.col + e0 + q) : -1;
+            const bool from_bits = COMPACT && kbits;  // keep decisions of the count pass
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 kq[q] = false;
                 if (e0 + q < b) {
-                    if ((unsigned)v[q] >= (unsigned long long)G.n) {
+                    if (from_bits) {
+                        kq[q] = (__ldg(kbits + ((e0 + q) >> 5)) >> ((e0 + q) & 31)) & 1u;
+                    } else if ((unsigned)v[q] >= (unsigned long long)G.n) {
                         atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
                     } else {
                         const int dv = __ldg(deg + G.vbase + v[q]);
@@ -253,6 +278,20 @@ __global__ void __launch_bounds__(HUB_THREADS)
                 keepc += kq[q];
             }
             if (!COMPACT) {
+                if (kbits) {
+                    // 8 lanes hold 32 consecutive entries as nibbles; the group's
+                    // first lane writes them as one word over the two it straddles
+                    const unsigned nib = (unsigned)kq[0] | (unsigned)kq[1] << 1 | (unsigned)kq[2] << 2 |
+                                         (unsigned)kq[3] << 3;
+                    unsigned word = nib << (4 * (lane & 7));
+#pragma unroll
+                    for (int o = 1; o < 8; o <<= 1) word |= __shfl_xor_sync(FULL, word, o);
+                    if ((lane & 7) == 0 && word) {
+                        const int sh = (int)(e0 & 31);
+                        atomicOr(kbits + (e0 >> 5), word << sh);
+                        if (sh) atomicOr(kbits + (e0 >> 5) + 1, word >> (32 - sh));
+                    }
+                }
                 total += keepc;
                 continue;
             }
@@ -450,8 +489,13 @@ __global__ void k_bin(const int32_t* __restrict__ dag_ptr, int64_t n, int warp_m
 template <typename Off, bool BATCH>
 cudaError_t orient_t(const GraphRef& one, const GraphRef* gs, int k, int64_t total, int32_t* deg, int32_t* kept,
                      long long* partial, int32_t* dag_ptr, int32_t* dag_col, int64_t dag_cap, int32_t* hubs,
-                     DevCounters* ctr, int num_sms, cudaStream_t st, long long* launches) {
+                     unsigned* kbits, int64_t kbits_words, DevCounters* ctr, int num_sms, cudaStream_t st,
+                     long long* launches) {
     if (total <= 0) return cudaSuccess;
+    if (kbits) {
+        const cudaError_t e = cudaMemsetAsync(kbits, 0, (size_t)kbits_words * 4, st);
+        if (e != cudaSuccess) return e;
+    }
     *launches += 8;
     const int hg = num_sms * 2;
     const int64_t groups = (total + 31) / 32;
@@ -462,17 +506,17 @@ cudaError_t orient_t(const GraphRef& one, const GraphRef* gs, int k, int64_t tot
     if (dg > num_sms * 16) dg = num_sms * 16;
     k_degree<Off, BATCH><<<dg, 256, 0, st>>>(one, gs, k, total, deg, hubs, ctr);
     k_orient<Off, false, BATCH><<<og, ORIENT_THREADS, 0, st>>>(one, gs, k, total, deg, kept, nullptr, nullptr, 0,
-                                                                ctr);
+                                                                kbits, ctr);
     k_orient_hub<Off, false, BATCH><<<hg, HUB_THREADS, 0, st>>>(one, gs, k, hubs, deg, kept, nullptr, nullptr, 0,
-                                                                 ctr);
+                                                                 kbits, ctr);
     const int nb = scan_blocks(total);
     k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(kept, total, partial);
     k_scan_top<<<1, SCAN_TOP_THREADS, 0, st>>>(partial, nb, dag_ptr, total, ctr);
     k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(kept, total, partial, dag_ptr);
     k_orient<Off, true, BATCH><<<og, ORIENT_THREADS, 0, st>>>(one, gs, k, total, deg, nullptr, dag_ptr, dag_col,
-                                                               dag_cap, ctr);
+                                                               dag_cap, kbits, ctr);
     k_orient_hub<Off, true, BATCH><<<hg, HUB_THREADS, 0, st>>>(one, gs, k, hubs, deg, nullptr, dag_ptr, dag_col,
-                                                                dag_cap, ctr);
+                                                                dag_cap, kbits, ctr);
     return cudaGetLastError();
 }
 
@@ -482,14 +526,15 @@ int scan_blocks(int64_t n) { return (int)((n + SCAN_TILE - 1) / SCAN_TILE); }
 
 cudaError_t launch_orient(const void* row_ptr, int offset_bits, const int32_t* col, int64_t n, int64_t nnz,
                           int32_t* deg, int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
-                          int64_t dag_cap, int32_t* hubs, DevCounters* ctr, int num_sms, cudaStream_t st,
-                          long long* launches) {
+                          int64_t dag_cap, int32_t* hubs, unsigned* kbits, DevCounters* ctr, int num_sms,
+                          cudaStream_t st, long long* launches) {
     const GraphRef one{row_ptr, col, n, nnz, 0};
+    const int64_t words = keep_bits_words(nnz);
     if (offset_bits == 64)
         return orient_t<long long, false>(one, nullptr, 1, n, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs,
-                                          ctr, num_sms, st, launches);
-    return orient_t<int32_t, false>(one, nullptr, 1, n, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs, ctr,
-                                    num_sms, st, launches);
+                                          kbits, words, ctr, num_sms, st, launches);
+    return orient_t<int32_t, false>(one, nullptr, 1, n, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs, kbits,
+                                    words, ctr, num_sms, st, launches);
 }
 
 cudaError_t launch_orient_batch(const GraphRef* graphs, int k, int offset_bits, int64_t total, int32_t* deg,
@@ -499,9 +544,9 @@ cudaError_t launch_orient_batch(const GraphRef* graphs, int k, int offset_bits, 
     const GraphRef none{nullptr, nullptr, 0, 0, 0};
     if (offset_bits == 64)
         return orient_t<long long, true>(none, graphs, k, total, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs,
-                                         ctr, num_sms, st, launches);
-    return orient_t<int32_t, true>(none, graphs, k, total, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs, ctr,
-                                   num_sms, st, launches);
+                                         nullptr, 0, ctr, num_sms, st, launches);
+    return orient_t<int32_t, true>(none, graphs, k, total, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs,
+                                   nullptr, 0, ctr, num_sms, st, launches);
 }
 
 cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* warp_desc,

@@ -77,10 +77,14 @@ constexpr int HUB_DEGREE = 1024;
 // warp_list: int32[n]; warp_desc: int2[n]; items: int2[item_cap].
 int scan_blocks(int64_t n);
 // hubs: int32[n] list of rows with degree > HUB_DEGREE (scratch).
+// kbits: NULL, or keep_bits_words(nnz) words of scratch: the count pass
+// records each entry's keep decision there and the compaction pass reads it
+// instead of gathering the neighbours' degrees a second time.
+inline int64_t keep_bits_words(int64_t nnz) { return (nnz >> 5) + 2; }
 cudaError_t launch_orient(const void* row_ptr, int offset_bits, const int32_t* col, int64_t n, int64_t nnz,
                           int32_t* deg, int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
-                          int64_t dag_cap, int32_t* hubs, DevCounters* ctr, int num_sms, cudaStream_t st,
-                          long long* launches);
+                          int64_t dag_cap, int32_t* hubs, unsigned* kbits, DevCounters* ctr, int num_sms,
+                          cudaStream_t st, long long* launches);
 
 // Orientation of k graphs at once (device array of GraphRef, bases ascending)
 // into one DAG over the padded global vertex space [0, total).
