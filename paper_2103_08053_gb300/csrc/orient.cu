@@ -69,27 +69,42 @@ constexpr int ORIENT_THREADS = 256;
 constexpr int ORIENT_WARPS = ORIENT_THREADS / 32;
 constexpr int ORIENT_UNROLL = 4;
 
-// COMPACT == false: kept[u] = out-degree. COMPACT == true: write dag_col.
-// Global row space [0, total); a batch pads every graph to a multiple of 32
-// rows, so a 32-row warp group never spans two graphs. deg, kept, dag_ptr
-// and the DAG's neighbour ids are global (vbase + local id).
+// Virtual-combination owner map (as in the counting kernels, Sec. 4.2):
+// lists held one per lane (inclusive prefix P, exclusive Pex, `listlane`
+// marks lanes holding a non-empty list, compacted to the low lanes); for the
+// window of combined indices [b, b+32), the list owning index b + lane.
+__device__ __forceinline__ int owner_of(int b, int P, int Pex, bool listlane, unsigned le) {
+    const int j0 = __popc(__ballot_sync(FULL, listlane && P <= b));
+    const unsigned bit = listlane ? __funnelshift_lc(0u, 1u, (unsigned)(Pex - b)) : 0u;
+    const unsigned starts = __reduce_or_sync(FULL, bit);
+    return j0 + __popc(starts & le) - (int)(starts & 1u);
+}
+
+// COMPACT == false: kept[u] = out-degree (and the keep bits). COMPACT == true:
+// write dag_col. Global row space [0, total); a batch pads every graph to a
+// multiple of 32 rows, so a 32-row warp group never spans two graphs. deg,
+// kept, dag_ptr and the DAG's neighbour ids are global (vbase + local id).
+//
+// A warp owns 32 consecutive rows. Its non-empty rows shorter than the hub
+// threshold are compacted to the low lanes (row id, start, length), and their
+// neighbour lists are walked as one virtually combined list, 32 entries per
+// window, coalesced; a lane finds the row of its entry with owner_of. The row
+// held by lane i counts its kept entries of a window with one popcount over
+// the window's ballot restricted to its lanes; in the compaction pass, a kept
+// entry's position is its row's next position (fetched from the row's lane)
+// plus the kept entries before it in the row's part of the window.
 template <typename Off, bool COMPACT, bool BATCH>
 __global__ void __launch_bounds__(ORIENT_THREADS)
     k_orient(GraphRef one, const GraphRef* __restrict__ gs, int k, int64_t total, const int32_t* __restrict__ deg,
              int32_t* __restrict__ kept, const int32_t* __restrict__ dag_ptr, int32_t* __restrict__ dag_col,
              int64_t dag_cap, unsigned* __restrict__ kbits, DevCounters* ctr) {
-    __shared__ long long s_st[ORIENT_WARPS][33];
-    __shared__ long long s_as[ORIENT_WARPS][32];
-    __shared__ int s_cnt[ORIENT_WARPS][32];
-    __shared__ int s_dp[ORIENT_WARPS][32];
+    __shared__ long long s_a[ORIENT_WARPS][32];
+    __shared__ int s_len[ORIENT_WARPS][32];
+    __shared__ int s_rid[ORIENT_WARPS][32];
     if (COMPACT && ctr->err) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned le = lanemask_le(lane), lt = lanemask_lt(lane);
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    long long* st = s_st[w];
-    long long* as = s_as[w];
-    int* cnt = s_cnt[w];
-    int* dp = s_dp[w];
     for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g * 32 < total; g += nw) {
         const GraphRef G = graph_of<BATCH>(g * 32, one, gs, k);
         const Off* row_ptr = static_cast<const Off*>(G.row_ptr);
@@ -97,6 +112,7 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
         const int64_t n = G.n, nnz = G.nnz, vb = G.vbase;
         const int64_t u0 = g * 32 - vb;  // local id of the group's first row
         const int nr = (int)(n - u0 < 32 ? (n - u0 > 0 ? n - u0 : 0) : 32);
+        const int64_t row0 = BATCH ? g * 32 : u0;  // index of the group's first row in kept / dag_ptr
         if (nr == 0) {  // padding rows of a batch
             if (!COMPACT) kept[g * 32 + lane] = 0;
             continue;
@@ -104,7 +120,7 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
         long long e = 0;
         if (lane == 0) e = (long long)row_ptr[u0 + nr];
         e = __shfl_sync(FULL, e, 0);
-        long long a = (lane < nr) ? (long long)row_ptr[u0 + lane] : e;
+        const long long a = (lane < nr) ? (long long)row_ptr[u0 + lane] : e;
         long long nx = __shfl_down_sync(FULL, a, 1);
         if (lane == 31) nx = e;
         const bool bad = (lane < nr) && (a < 0 || nx < a || nx > nnz);
@@ -112,42 +128,49 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
             if (lane == 0) atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
             continue;
         }
-        // hub rows (left to the hub kernel) take no room in the warp's walk:
-        // st holds virtual starts over the other rows, as their real starts
-        const long long len = (lane < nr && nx - a <= HUB_DEGREE) ? nx - a : 0;
-        long long vin = len;
+        const long long len = nx - a;
+        // rows walked here: non-empty and not hubs (the hub kernel takes those)
+        const bool walk = lane < nr && len > 0 && len <= HUB_DEGREE;
+        if (!COMPACT && (BATCH || lane < nr) && !walk) kept[row0 + lane] = 0;  // hub rows: rewritten later
+        const unsigned wm = __ballot_sync(FULL, walk);
+        if (wm == 0) continue;
+        const bool hubless = __ballot_sync(FULL, lane < nr && len > HUB_DEGREE) == 0;
+        const int c = __popc(wm);
+        if (walk) {
+            const int p = __popc(wm & lt);
+            s_a[w][p] = a;
+            s_len[w][p] = (int)len;
+            s_rid[w][p] = lane;
+        }
+        __syncwarp();
+        const bool lst = lane < c;
+        const long long ca = lst ? s_a[w][lane] : 0;
+        const int cl = lst ? s_len[w][lane] : 0;
+        const int rid = lst ? s_rid[w][lane] : 0;
+        __syncwarp();
+        int P = cl;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const long long t = __shfl_up_sync(FULL, vin, o);
-            if (lane >= o) vin += t;
+            const int t = __shfl_up_sync(FULL, P, o);
+            if (lane >= o) P += t;
         }
-        st[lane] = vin - len;
-        as[lane] = a;
-        if (lane == 31) st[32] = vin;
-        // without hub rows the walk is the plain concatenation starting at gb0
-        const bool hubless = __shfl_sync(FULL, vin, 31) == e - __shfl_sync(FULL, a, 0);
-        const long long gb0 = __shfl_sync(FULL, a, 0);
-        cnt[lane] = 0;
-        if (COMPACT) dp[lane] = (lane < nr) ? dag_ptr[g * 32 + lane] : 0;
-        __syncwarp();
-        const long long gb = 0, ge = st[32];
-        int r = 0;
-        for (long long base = gb; base < ge; base += 32 * ORIENT_UNROLL) {
-            // issue every load of the step first: ORIENT_UNROLL col reads, then
-            // their degree gathers, so each lane has that many requests in flight
-            int vq[ORIENT_UNROLL], dq[ORIENT_UNROLL];
+        const int tot = __shfl_sync(FULL, P, 31);
+        const int Pex = P - cl;
+        const long long bias = ca - Pex;  // col index of combined entry f of this row: bias + f
+        int cnt = (COMPACT && lst) ? dag_ptr[row0 + rid] : 0;  // compaction: the row's next output position
+        for (int b0 = 0; b0 < tot; b0 += 32 * ORIENT_UNROLL) {
+            // every load of the step first: ORIENT_UNROLL col reads, then their
+            // degree gathers, so each lane has that many requests in flight
+            int vq[ORIENT_UNROLL], dq[ORIENT_UNROLL], oq[ORIENT_UNROLL];
             long long atq[ORIENT_UNROLL];
 #pragma unroll
             for (int q = 0; q < ORIENT_UNROLL; ++q) {
-                const long long f = base + 32 * q + lane;
-                long long at = gb0 + f;
-                if (!hubless && f < ge) {
-                    int rq = r;
-                    while (st[rq + 1] <= f) ++rq;
-                    at = as[rq] + (f - st[rq]);
-                }
-                atq[q] = at;
-                vq[q] = (f < ge) ? __ldg(col + at) : -1;
+                const int bw = b0 + 32 * q;
+                const int o = owner_of(bw, P, Pex, lst, le) & 31;
+                oq[q] = o;
+                const int f = bw + lane;
+                atq[q] = __shfl_sync(FULL, bias, o) + f;
+                vq[q] = (f < tot) ? __ldg(col + atq[q]) : -1;
             }
             // the compaction pass reads the count pass's keep bits instead of
             // gathering the neighbours' degrees again
@@ -157,29 +180,30 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
                 dq[q] = (gather && (unsigned)vq[q] < (unsigned long long)n) ? __ldg(deg + vb + vq[q]) : 0;
 #pragma unroll
             for (int q = 0; q < ORIENT_UNROLL; ++q) {
-                const long long f = base + 32 * q + lane;
-                const bool act = f < ge;
-                bool keep = false;
+                const int bw = b0 + 32 * q;
+                if (bw >= tot) break;
+                const int f = bw + lane;
+                const bool act = f < tot;
+                const int o = oq[q];
+                const int du = __shfl_sync(FULL, cl, o);
+                const int ur = __shfl_sync(FULL, rid, o);
                 const int v = vq[q];
+                bool keep = false;
                 if (act) {
-                    while (st[r + 1] <= f) ++r;
                     if (!gather) {
                         keep = (__ldg(kbits + (atq[q] >> 5)) >> (atq[q] & 31)) & 1u;
                     } else if ((unsigned)v >= (unsigned long long)n) {
                         atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
                     } else {
-                        const int du = (int)(st[r + 1] - st[r]);  // rows in the walk are not hubs
                         const int dv = dq[q];
-                        keep = (dv > du) || (dv == du && (int64_t)v > u0 + r);
+                        keep = (dv > du) || (dv == du && (int64_t)v > u0 + ur);
                     }
                 }
                 const unsigned km = __ballot_sync(FULL, keep);
-                const unsigned am = __ballot_sync(FULL, act);
-                if (am == 0) break;
                 if (!COMPACT && kbits) {
-                    // keep bit of entry `at` -> kbits; a hubless walk covers 32
-                    // consecutive entries, whose bits lane 0 writes as one word
-                    // split over the two words it straddles
+                    // keep bit of entry `at` -> kbits; without hub rows the window
+                    // covers 32 consecutive entries, whose bits lane 0 writes as
+                    // one word split over the two words it straddles
                     if (hubless) {
                         if (lane == 0 && km) {
                             const long long a0 = atq[q];
@@ -191,35 +215,25 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
                         atomicOr(kbits + (atq[q] >> 5), 1u << (atq[q] & 31));
                     }
                 }
-                const int rp = __shfl_up_sync(FULL, r, 1);
-                const int rn = __shfl_down_sync(FULL, r, 1);
-                const bool seg_start = act && (lane == 0 || rp != r);
-                const bool seg_end = act && (lane == 31 || !((am >> (lane + 1)) & 1u) || rn != r);
-                const unsigned sm = __ballot_sync(FULL, seg_start);
-                unsigned segbits = 0;
-                if (act) {
-                    const int first = 31 - __clz(sm & le);
-                    segbits = ~((1u << first) - 1u);
+                // lanes of this window holding entries of the row of lane `lane`
+                const int lo = max(Pex, bw) - bw, hi = min(P, bw + 32) - bw;
+                const unsigned rowbits =
+                    (lst && lo < hi) ? ((hi >= 32 ? FULL : ((1u << hi) - 1u)) & ~((1u << lo) - 1u)) : 0u;
+                if (COMPACT) {
+                    const int next = __shfl_sync(FULL, cnt, o);  // the row's next output position
+                    const int first = __shfl_sync(FULL, lo, o);  // the row's first lane in the window
+                    if (keep) {
+                        const long long pos = (long long)next + __popc(km & lt & ~((1u << first) - 1u));
+                        if (pos < dag_cap)
+                            dag_col[pos] = (int32_t)(vb + v);
+                        else
+                            atomicOr(&ctr->err, ERRBIT_DAG_OVERFLOW);
+                    }
                 }
-                if (COMPACT && keep) {
-                    const long long pos = (long long)dp[r] + cnt[r] + __popc(km & lt & segbits);
-                    if (pos < dag_cap)
-                        dag_col[pos] = (int32_t)(vb + v);
-                    else
-                        atomicOr(&ctr->err, ERRBIT_DAG_OVERFLOW);
-                }
-                __syncwarp();
-                if (seg_end) cnt[r] += __popc(km & le & segbits);
-                __syncwarp();
+                cnt += __popc(km & rowbits);
             }
         }
-        if (!COMPACT) {
-            if (BATCH)
-                kept[g * 32 + lane] = cnt[lane];  // rows past nr of the graph are padding: 0
-            else if (lane < nr)
-                kept[u0 + lane] = cnt[lane];
-        }
-        __syncwarp();
+        if (!COMPACT && lst) kept[row0 + rid] = cnt;
     }
 }
 
