@@ -69,7 +69,13 @@ static_assert(VC_UNROLL == 4, "the bitmap owner path reads four window words at 
 #endif
 
 #ifndef BLOCK_PIECE
-#define BLOCK_PIECE 512  // combined 2-hop indices per piece of a thread-block item
+#define BLOCK_PIECE 512  // combined 2-hop indices per piece of a thread-block item (fixed pieces)
+#endif
+#ifndef BLOCK_ADAPTIVE_PIECE
+#define BLOCK_ADAPTIVE_PIECE 1  // 1: pieces sized so that each warp of the block gets about two
+#endif
+#ifndef BLOCK_SLOTS
+#define BLOCK_SLOTS 4  // slots per bucket of the thread-block tables (2: overflow chains at load 1/2 cost more)
 #endif
 
 constexpr int STAGE_INTS = 224;        // warp workers: 4 x 32 compaction lanes | 32 slot hits | 64-word bitmap
@@ -154,14 +160,22 @@ __device__ __forceinline__ int insert_b4(int* sm, int tab, int lenw, int lgB, in
 
 // Same claim with one 32-bit length word per bucket (thread-block tables,
 // whose buckets can see more than 255 claims).
-template <int HM>
+// With SL = 2 the lengths are 16-bit, two per word (a part holds at most
+// 2^16 - 1 keys, so a length never carries into its neighbour).
+template <int HM, int SL = 4>
 __device__ __forceinline__ void insert_b4w(int* sm, int tab, int lenw, int lgB, int w) {
     const int mask = (1 << lgB) - 1;
     int h = bucket_of<HM>(w, lgB);
     for (int s = 0; s <= mask; ++s) {
-        const int slot = atomicAdd(sm + lenw + h, 1);
-        if (slot < 4) {
-            sm[tab + 4 * h + slot] = w;
+        int slot;
+        if (SL == 4) {
+            slot = atomicAdd(sm + lenw + h, 1);
+        } else {
+            const int sh = 16 * (h & 1);
+            slot = (int)((atomicAdd(reinterpret_cast<unsigned*>(sm + lenw + (h >> 1)), 1u << sh) >> sh) & 0xffffu);
+        }
+        if (slot < SL) {
+            sm[tab + SL * h + slot] = w;
             return;
         }
         h = (h + 1) & mask;
@@ -478,7 +492,7 @@ __device__ __forceinline__ uint32_t vc_pack_quad(int s, int l, int td, const int
 // quad indices [skip, min(limit, total)) are dealt one per lane, QUAD_UNROLL
 // per step; slots outside their list are masked; a key whose bucket is full
 // and did not match walks the overflow chain. *done = quads processed.
-template <int HM>
+template <int HM, int SL>
 __device__ __forceinline__ uint32_t vc_range_quad(int s, int e, int nq, int tab, int lgB, int skip, int limit,
                                                   const int* sm, const int32_t* __restrict__ dag_col, int m, int lane,
                                                   int* stage, int* done) {
@@ -545,15 +559,15 @@ __device__ __forceinline__ uint32_t vc_range_quad(int s, int e, int nq, int tab,
             for (int j = 0; j < 4; ++j) {
                 if (j >= lo[q] && j < hi[q]) {
                     const int h = bucket_of<HM>(key[j], lgB);
-                    const int4 b4 = *reinterpret_cast<const int4*>(sm + tab + 4 * h);
-                    const int hit = match4(b4, key[j]);
+                    const Bucket<SL> b = Bucket<SL>::at(sm, tab, h);
+                    const int hit = b.match(key[j]);
                     hits += hit;
-                    more |= (!hit && b4.w != EMPTY) << j;
+                    more |= (!hit && b.full()) << j;
                 }
             }
             if (__any_sync(FULL, more)) {
                 for (int j = 0; j < 4; ++j)
-                    if ((more >> j) & 1) hits += probe_chain<4>(sm, tab, mask, bucket_of<HM>(key[j], lgB), key[j]);
+                    if ((more >> j) & 1) hits += probe_chain<SL>(sm, tab, mask, bucket_of<HM>(key[j], lgB), key[j]);
             }
         }
     }
@@ -808,8 +822,11 @@ __global__ void __launch_bounds__(1024, 1)
         uint32_t h = 0;
         for (int p0 = 0; p0 < k && W > 0; p0 += part_max) {
             const int pk = min(part_max, k - p0);
+            // 4 * nextpow2(part) slots in buckets of BLOCK_SLOTS, then one
+            // length word per 4 slots (32-bit lengths for 4-slot buckets,
+            // two 16-bit lengths for 2-slot buckets)
             const int B = next_pow2(pk < 32 ? 32 : pk);
-            const int lgB = 31 - __clz(B);
+            const int lgB = 31 - __clz(B) + (BLOCK_SLOTS == 2 ? 1 : 0);  // log2 of the bucket count
             const long long t_build = timing ? clock64() : 0;
             int* tab = smem + table_off;
             const int lenw = table_off + 4 * B;
@@ -819,11 +836,15 @@ __global__ void __launch_bounds__(1024, 1)
             if (threadIdx.x == 0) s_piece = 0;
             __syncthreads();
             for (int t = threadIdx.x; t < pk; t += blockDim.x)
-                insert_b4w<HM>(smem, table_off, lenw, lgB, __ldg(dag_col + a + p0 + t));
+                insert_b4w<HM, BLOCK_SLOTS>(smem, table_off, lenw, lgB, __ldg(dag_col + a + p0 + t));
             __syncthreads();
             const long long t_probe = timing ? clock64() : 0;
             if (timing) cyc_b += t_probe - t_build;
-            const int piece = quad ? PIECE / 4 : PIECE;  // combined units (quads or keys) per piece
+            // combined units (quads or keys) per piece: about 2 pieces per warp
+            // (pieces are equal, so that balances), at least one 32-unit window
+            const int unit_min = quad ? PIECE / 4 : PIECE;
+            int piece = (W + 2 * nw - 1) / (2 * nw);
+            piece = BLOCK_ADAPTIVE_PIECE ? (piece < 32 ? 32 : (piece + 31) & ~31) : unit_min;
             for (;;) {
                 int pc = 0;
                 if (lane == 0) pc = atomicAdd(&s_piece, 1);
@@ -844,11 +865,11 @@ __global__ void __launch_bounds__(1024, 1)
                     int done = 0;
                     if (quad) {
                         const int ej = j < cnt ? E[j] : 0;
-                        h += vc_range_quad<HM>(sj, ej, uj, table_off, lgB, F - base_flat, F1 - base_flat, smem,
-                                               dag_col, m, lane, stage, &done);
+                        h += vc_range_quad<HM, BLOCK_SLOTS>(sj, ej, uj, table_off, lgB, F - base_flat,
+                                                            F1 - base_flat, smem, dag_col, m, lane, stage, &done);
                     } else {
-                        h += vc_range_b4<false, HM>(sj, uj, table_off, lgB, 0, F - base_flat, F1 - base_flat, smem,
-                                                    dag_col, lane, stage, &done);
+                        h += vc_range_b4<false, HM, BLOCK_SLOTS>(sj, uj, table_off, lgB, 0, F - base_flat,
+                                                                 F1 - base_flat, smem, dag_col, lane, stage, &done);
                     }
                     F += done;
                 }
