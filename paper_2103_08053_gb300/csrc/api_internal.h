@@ -64,6 +64,8 @@ struct TimedCall {
 // and the buffers stay the same. Used by tc_count_batch and by serving rounds.
 struct BatchRunner {
     cudaStream_t stream = nullptr;
+    int priority = 0;          // stream priority (init); 0 = default
+    float grid_share = 1.0f;   // fraction of the persistent counting grids this runner launches
     cudaEvent_t ev_in = nullptr, ev_done = nullptr;
     Workspace ws;
     DevBuf graphs, per_vertex, counts, dag_ptr, dag_col;

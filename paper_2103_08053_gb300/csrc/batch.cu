@@ -41,7 +41,8 @@ __global__ void k_segsum(const unsigned long long* __restrict__ per_vertex, cons
 // ---------------------------------------------------------------- BatchRunner
 
 tc_status BatchRunner::init(tc_ctx* ctx) {
-    tc_status s = cuda_status(ctx, cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    tc_status s = cuda_status(ctx, cudaStreamCreateWithPriority(&stream, cudaStreamNonBlocking, priority),
+                              "cudaStreamCreateWithPriority");
     if (!s) s = cuda_status(ctx, cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming), "cudaEventCreate");
     if (!s) s = cuda_status(ctx, cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming), "cudaEventCreate");
     return s;
@@ -157,10 +158,15 @@ tc_status BatchRunner::enqueue(tc_ctx* ctx) {
         e = launch_bin((const int32_t*)dag_ptr.p, total, ctx->cfg, (int32_t*)ws.warp_list.p, (int2*)ws.warp_desc.p,
                        (int2*)ws.items.p, (int64_t)(ws.items.bytes / sizeof(int2)), ctr, ctx->num_sms, stream,
                        &nl);
+    CountCfg cfg = ctx->cfg;
+    if (grid_share < 1.0f) {  // leave SMs to runners on other streams
+        cfg.warp_grid = cfg.warp_grid * grid_share < 1.0f ? 1 : (int)(cfg.warp_grid * grid_share);
+        cfg.block_grid = cfg.block_grid * grid_share < 1.0f ? 1 : (int)(cfg.block_grid * grid_share);
+    }
     if (e == cudaSuccess)
         e = launch_count((const int32_t*)dag_ptr.p, (const int32_t*)dag_col.p, total,
                          (const int32_t*)ws.warp_list.p, (const int2*)ws.warp_desc.p, (const int2*)ws.items.p,
-                         (unsigned long long*)per_vertex.p, ctx->cfg, ctr, stream, &nl);
+                         (unsigned long long*)per_vertex.p, cfg, ctr, stream, &nl);
     if (e == cudaSuccess) {
         k_segsum<<<k, 256, 0, stream>>>((const unsigned long long*)per_vertex.p, (const GraphRef*)graphs.p,
                                         (unsigned long long*)counts.p);

@@ -9,12 +9,17 @@
 //      at submission with TC_ERR_BUSY;
 //   2. completion: a finished round's per-graph counts are handed to its
 //      tickets and the round's arena memory is freed, which admits more;
-//   3. launch: whenever one of kRounds round slots is idle and admitted
-//      requests wait, they form a round: their CSRs are copied to the device on
+//   3. launch: whenever a round slot is idle and admitted requests of its
+//      class wait, they form a round: their CSRs are copied to the device on
 //      the round's stream and counted by the batched path (one padded
 //      orientation + one counting pass, batch.cu). Rounds run on separate
 //      streams, so a round formed from requests that arrived while others were
 //      on the GPU overlaps with them.
+// Two request classes keep large graphs from holding up small ones: a graph
+// with more than kLargeEntries CSR entries is large and runs alone in the
+// large slot, whose stream has the lowest priority and whose persistent
+// counting kernels take kLargeGridShare of the SMs; small graphs share the
+// other slots, whose streams have the highest priority.
 // Each request's count is that of its own graph, whatever else is in its
 // round (the batch lays graphs out disjointly).
 #include <chrono>
@@ -29,7 +34,10 @@ namespace tcg {
 
 namespace {
 
-constexpr int kRounds = 3;                    // round slots (streams) in flight
+constexpr int kRounds = 4;                    // round slots (streams) in flight; the last is for large graphs
+constexpr int kLargeSlot = kRounds - 1;
+constexpr long long kLargeEntries = 1ll << 24;  // n + nnz above this: a large request
+constexpr float kLargeGridShare = 0.75f;
 constexpr int kMaxRoundGraphs = 4096;         // graphs per round
 constexpr long long kMaxRoundEntries = 1ll << 30;  // CSR entries per round
 constexpr size_t kAlign = 256;
@@ -192,25 +200,32 @@ void worker_loop(tc_ctx* ctx) {
             S.admitted.push_back(q);
             S.queue.pop_front();
         }
-        // launch: idle round slots take the admitted requests
+        // launch: idle round slots take the admitted requests of their class
         bool launched = false;
-        for (Round& r : S.rounds) {
+        for (int slot = 0; slot < kRounds; ++slot) {
+            Round& r = S.rounds[slot];
+            const bool large_slot = slot == kLargeSlot;
             if (r.busy || S.admitted.empty()) continue;
-            // a round holds requests of one offset width, oldest first
-            const int bits = S.admitted.front()->bits;
+            // a round holds requests of one class and one offset width, oldest
+            // first; a large round holds one graph
+            int bits = 0;
             long long entries = 0;
             r.reqs.clear();
             for (size_t i = 0; i < S.admitted.size() && (int)r.reqs.size() < kMaxRoundGraphs;) {
                 Request* q = S.admitted[i];
                 const long long e2 = entries + q->nnz + q->n;
-                if (q->bits != bits || (!r.reqs.empty() && e2 > kMaxRoundEntries)) {
+                const bool large = q->nnz + q->n > kLargeEntries;
+                if (large != large_slot || (bits && q->bits != bits) || (!r.reqs.empty() && e2 > kMaxRoundEntries)) {
                     ++i;
                     continue;
                 }
+                bits = q->bits;
                 entries = e2;
                 r.reqs.push_back(q);
                 S.admitted.erase(S.admitted.begin() + (long)i);
+                if (large_slot) break;
             }
+            if (r.reqs.empty()) continue;
             for (Request* q : r.reqs) q->state = ReqState::Running;
             r.busy = true;
             lk.unlock();
@@ -259,7 +274,13 @@ tc_status serve_start(tc_ctx* ctx) {
         S->arena.reset(ctx->mem_budget);
         ctx->held_bytes += (long long)ctx->mem_budget;
     }
+    int least = 0, greatest = 0;
+    if (!s)
+        s = cuda_status(ctx, cudaDeviceGetStreamPriorityRange(&least, &greatest),
+                        "cudaDeviceGetStreamPriorityRange");
     for (int i = 0; i < kRounds && !s; ++i) {
+        S->rounds[i].runner.priority = i == kLargeSlot ? least : greatest;
+        S->rounds[i].runner.grid_share = i == kLargeSlot ? kLargeGridShare : 1.0f;
         s = S->rounds[i].runner.init(ctx);
         if (!s) s = cuda_status(ctx, cudaEventCreateWithFlags(&S->rounds[i].done, cudaEventDisableTiming),
                                 "cudaEventCreate");

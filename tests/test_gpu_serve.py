@@ -120,3 +120,18 @@ def test_borrowed_submission(T):
     with T.Context(0, mem_budget=1 << 30) as c:
         tickets = [c.submit_borrowed(*h) for h in keep]
         assert wait_all(c, tickets) == want
+
+
+def test_large_and_small_classes(T):
+    # graphs with more than 2^24 CSR entries run alone in the large slot (low
+    # priority, part of the SMs); small ones keep flowing through the others
+    big = [G.rmat(20, 16, seed=40 + i) for i in range(2)]
+    assert all(g.n + g.nnz > 1 << 24 for g in big)
+    small = [G.batch_graph(13, i) for i in range(60)]
+    want_big = [oracle.count(g) for g in big]
+    want_small = [oracle.count(g) for g in small]
+    with T.Context(0, mem_budget=4 << 30) as c:
+        tb = [c.submit(*host(g)) for g in big]
+        ts = [c.submit(*host(g)) for g in small]
+        assert wait_all(c, ts) == want_small
+        assert wait_all(c, tb) == want_big
