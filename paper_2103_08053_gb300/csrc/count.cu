@@ -74,6 +74,9 @@ static_assert(VC_UNROLL == 4, "the bitmap owner path reads four window words at 
 #ifndef BLOCK_ADAPTIVE_PIECE
 #define BLOCK_ADAPTIVE_PIECE 1  // 1: pieces sized so that each warp of the block gets about two
 #endif
+#ifndef PACK_STRIDED
+#define PACK_STRIDED 1  // 1: a pop takes warp-list entries S apart (see k_count_pack)
+#endif
 #ifndef BLOCK_SLOTS
 #define BLOCK_SLOTS 4  // slots per bucket of the thread-block tables (2: overflow chains at load 1/2 cost more)
 #endif
@@ -631,15 +634,27 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
     int* stage = smem + area + area_ints;
     const int nlist = ctr->n_warp;
     unsigned long long acc = 0;
+    // A pop takes up to `pop` vertices of the warp list, fewer when the list
+    // is short, so that there are at least 4 pops per warp of the grid.
+    // PACK_STRIDED: pop q takes entries q, q + S, q + 2S, ... (S =
+    // ceil(nlist / pop)), so every pop is a sample of the whole list and pops
+    // cost about the same even when vertex cost follows the list order (R-MAT
+    // ids: the heaviest vertices first).
+    {
+        const int per = nlist / (4 * (int)(gridDim.x * (blockDim.x >> 5)));
+        pop = per < 1 ? 1 : (per < pop ? per : pop);
+    }
+    const int S = (nlist + pop - 1) / pop;
     for (;;) {
         int i0 = 0;
-        if (lane == 0) i0 = atomicAdd(&ctr->q_warp, pop);
+        if (lane == 0) i0 = atomicAdd(&ctr->q_warp, PACK_STRIDED ? 1 : pop);
         i0 = __shfl_sync(FULL, i0, 0);
-        if (i0 >= nlist) break;
-        const int cnt = min(pop, nlist - i0);
+        if (PACK_STRIDED ? i0 >= S : i0 >= nlist) break;
+        const int cnt = PACK_STRIDED ? min(pop, (nlist - i0 + S - 1) / S) : min(pop, nlist - i0);
+        const int li = PACK_STRIDED ? i0 + lane * S : i0 + lane;  // this lane's warp-list entry
         int a = 0, k = 0;
         if (lane < cnt) {
-            const int2 d = __ldg(desc + i0 + lane);
+            const int2 d = __ldg(desc + li);
             a = d.x;
             k = d.y;
         }
@@ -748,7 +763,7 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
             if (timing) cyc_p += clock64() - t_probe;
             if (PER_VERTEX) {
                 __syncwarp();
-                if (in) per_vertex[__ldg(warp_list + i0 + lane)] = (unsigned long long)stage[128 + lane];
+                if (in) per_vertex[__ldg(warp_list + li)] = (unsigned long long)stage[128 + lane];
             }
             __syncwarp();
             p0 = p1;

@@ -62,6 +62,7 @@ __global__ void k_degree(GraphRef one, const GraphRef* __restrict__ gs, int k, i
         }
         deg[u] = (int32_t)d;
         if (d > HUB_DEGREE) hubs[atomicAdd(&ctr->n_hub, 1)] = (int32_t)u;
+        else if (d > MID_DEGREE) hubs[total - 1 - atomicAdd(&ctr->n_mid, 1)] = (int32_t)u;  // from the back
     }
 }
 
@@ -130,11 +131,11 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
         }
         const long long len = nx - a;
         // rows walked here: non-empty and not hubs (the hub kernel takes those)
-        const bool walk = lane < nr && len > 0 && len <= HUB_DEGREE;
+        const bool walk = lane < nr && len > 0 && len <= MID_DEGREE;
         if (!COMPACT && (BATCH || lane < nr) && !walk) kept[row0 + lane] = 0;  // hub rows: rewritten later
         const unsigned wm = __ballot_sync(FULL, walk);
         if (wm == 0) continue;
-        const bool hubless = __ballot_sync(FULL, lane < nr && len > HUB_DEGREE) == 0;
+        const bool hubless = __ballot_sync(FULL, lane < nr && len > MID_DEGREE) == 0;
         const int c = __popc(wm);
         if (walk) {
             const int p = __popc(wm & lt);
@@ -238,7 +239,9 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
 }
 
 // Orientation of hub rows (degree > HUB_DEGREE): one block per row, rows
-// taken from the hub list with an atomic cursor. A tile is 4 consecutive
+// taken from the hub list with an atomic cursor; then of mid rows
+// (MID_DEGREE < degree <= HUB_DEGREE), one warp per row, so that a 32-row
+// group of long rows does not hold up a whole orientation pass. A tile is 4 consecutive
 // entries per thread (loads issued together); the count pass reduces the
 // kept entries of the row, the compaction pass places them in input order
 // with a block-wide exclusive scan per tile.
@@ -246,7 +249,7 @@ constexpr int HUB_THREADS = 512;
 
 template <typename Off, bool COMPACT, bool BATCH>
 __global__ void __launch_bounds__(HUB_THREADS)
-    k_orient_hub(GraphRef one, const GraphRef* __restrict__ gs, int k, const int32_t* __restrict__ hubs,
+    k_orient_hub(GraphRef one, const GraphRef* __restrict__ gs, int k, int64_t total, const int32_t* __restrict__ hubs,
                  const int32_t* __restrict__ deg, int32_t* __restrict__ kept, const int32_t* __restrict__ dag_ptr,
                  int32_t* __restrict__ dag_col, int64_t dag_cap, unsigned* __restrict__ kbits, DevCounters* ctr) {
     __shared__ int s_row, s_carry;
@@ -356,6 +359,69 @@ __global__ void __launch_bounds__(HUB_THREADS)
             }
         }
         __syncthreads();
+    }
+    // mid rows (MID_DEGREE < degree <= HUB_DEGREE): one warp each, taken from
+    // the back of the list with an atomic cursor, 64 entries per step
+    const int nmid = ctr->n_mid;
+    const unsigned lt = (1u << lane) - 1u;
+    for (;;) {
+        int mi = 0;
+        if (lane == 0) mi = atomicAdd(&ctr->q_mid[COMPACT ? 1 : 0], 1);
+        mi = __shfl_sync(FULL, mi, 0);
+        if (mi >= nmid) break;
+        const int64_t ug = hubs[total - 1 - mi];
+        const GraphRef G = graph_of<BATCH>(ug, one, gs, k);
+        const int64_t u = ug - G.vbase;
+        const Off* rp = static_cast<const Off*>(G.row_ptr);
+        const long long ra = (long long)rp[u];  // checked by k_degree
+        const int rl = (int)((long long)rp[u + 1] - ra);
+        int rc = COMPACT ? dag_ptr[ug] : 0;  // compaction: next output position; count: kept so far
+        for (int b = 0; b < rl; b += 64) {
+            const int f0 = b + lane, f1 = b + 32 + lane;
+            const int v0 = f0 < rl ? __ldg(G.col + ra + f0) : -1;
+            const int v1 = f1 < rl ? __ldg(G.col + ra + f1) : -1;
+            bool k0 = false, k1 = false;
+            if (COMPACT && kbits) {
+                if (f0 < rl) k0 = (__ldg(kbits + ((ra + f0) >> 5)) >> ((ra + f0) & 31)) & 1u;
+                if (f1 < rl) k1 = (__ldg(kbits + ((ra + f1) >> 5)) >> ((ra + f1) & 31)) & 1u;
+            } else {
+                const bool ok0 = (unsigned)v0 < (unsigned long long)G.n, ok1 = (unsigned)v1 < (unsigned long long)G.n;
+                const int d0 = ok0 ? __ldg(deg + G.vbase + v0) : 0;
+                const int d1 = ok1 ? __ldg(deg + G.vbase + v1) : 0;
+                if ((f0 < rl && !ok0) || (f1 < rl && !ok1)) atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
+                k0 = ok0 && ((d0 > rl) || (d0 == rl && (int64_t)v0 > u));
+                k1 = ok1 && ((d1 > rl) || (d1 == rl && (int64_t)v1 > u));
+            }
+            const unsigned km0 = __ballot_sync(FULL, k0), km1 = __ballot_sync(FULL, k1);
+            if (!COMPACT && kbits && lane == 0) {
+                // 64 consecutive entries from ra + b: bits km0, then km1
+                const long long a0 = ra + b;
+                const int sh = (int)(a0 & 31);
+                unsigned* wd = kbits + (a0 >> 5);
+                if (sh == 0) {
+                    if (km0) atomicOr(wd, km0);
+                    if (km1) atomicOr(wd + 1, km1);
+                } else {
+                    if (km0 << sh) atomicOr(wd, km0 << sh);
+                    if ((km0 >> (32 - sh)) | (km1 << sh)) atomicOr(wd + 1, (km0 >> (32 - sh)) | (km1 << sh));
+                    if (km1 >> (32 - sh)) atomicOr(wd + 2, km1 >> (32 - sh));
+                }
+            }
+            if (COMPACT) {
+                const long long p0 = (long long)rc + __popc(km0 & lt);
+                const long long p1 = (long long)rc + __popc(km0) + __popc(km1 & lt);
+                if (k0) {
+                    if (p0 < dag_cap) dag_col[p0] = (int32_t)(G.vbase + v0);
+                    else atomicOr(&ctr->err, ERRBIT_DAG_OVERFLOW);
+                }
+                if (k1) {
+                    if (p1 < dag_cap) dag_col[p1] = (int32_t)(G.vbase + v1);
+                    else atomicOr(&ctr->err, ERRBIT_DAG_OVERFLOW);
+                }
+            }
+            rc += __popc(km0) + __popc(km1);
+        }
+        if (!COMPACT && lane == 0) kept[ug] = rc;
     }
 }
 
@@ -521,7 +587,7 @@ cudaError_t orient_t(const GraphRef& one, const GraphRef* gs, int k, int64_t tot
     k_degree<Off, BATCH><<<dg, 256, 0, st>>>(one, gs, k, total, deg, hubs, ctr);
     k_orient<Off, false, BATCH><<<og, ORIENT_THREADS, 0, st>>>(one, gs, k, total, deg, kept, nullptr, nullptr, 0,
                                                                 kbits, ctr);
-    k_orient_hub<Off, false, BATCH><<<hg, HUB_THREADS, 0, st>>>(one, gs, k, hubs, deg, kept, nullptr, nullptr, 0,
+    k_orient_hub<Off, false, BATCH><<<hg, HUB_THREADS, 0, st>>>(one, gs, k, total, hubs, deg, kept, nullptr, nullptr, 0,
                                                                  kbits, ctr);
     const int nb = scan_blocks(total);
     k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(kept, total, partial);
@@ -529,7 +595,7 @@ cudaError_t orient_t(const GraphRef& one, const GraphRef* gs, int k, int64_t tot
     k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(kept, total, partial, dag_ptr);
     k_orient<Off, true, BATCH><<<og, ORIENT_THREADS, 0, st>>>(one, gs, k, total, deg, nullptr, dag_ptr, dag_col,
                                                                dag_cap, kbits, ctr);
-    k_orient_hub<Off, true, BATCH><<<hg, HUB_THREADS, 0, st>>>(one, gs, k, hubs, deg, nullptr, dag_ptr, dag_col,
+    k_orient_hub<Off, true, BATCH><<<hg, HUB_THREADS, 0, st>>>(one, gs, k, total, hubs, deg, nullptr, dag_ptr, dag_col,
                                                                 dag_cap, kbits, ctr);
     return cudaGetLastError();
 }

@@ -36,7 +36,9 @@ struct DevCounters {
     int err;                   // ERRBIT_* flags
     int n_hub;                 // rows with degree > HUB_DEGREE (orientation by thread blocks)
     int q_hub[2];              // hub-row cursors of the two orientation passes
-    int pad[14];
+    int n_mid;                 // rows with MID_DEGREE < degree <= HUB_DEGREE (orientation by warps)
+    int q_mid[2];
+    int pad[11];
 };
 static_assert(sizeof(DevCounters) == 128, "DevCounters layout");
 
@@ -73,10 +75,13 @@ struct GraphRef {
 // Rows longer than this are oriented by one thread block each instead of
 // inside a 32-row warp group.
 constexpr int HUB_DEGREE = 1024;
+// Rows longer than this (and not hubs) are oriented by one warp each.
+constexpr int MID_DEGREE = 128;
 // deg, kept: int32[n]; partial: int64[scan_blocks(n)+1]; dag_ptr: int32[n+1];
 // warp_list: int32[n]; warp_desc: int2[n]; items: int2[item_cap].
 int scan_blocks(int64_t n);
-// hubs: int32[n] list of rows with degree > HUB_DEGREE (scratch).
+// hubs: int32[n] scratch: rows with degree > HUB_DEGREE from the front, rows
+// with MID_DEGREE < degree <= HUB_DEGREE from the back.
 // kbits: NULL, or keep_bits_words(nnz) words of scratch: the count pass
 // records each entry's keep decision there and the compaction pass reads it
 // instead of gathering the neighbours' degrees a second time.

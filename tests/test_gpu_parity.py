@@ -124,6 +124,24 @@ def test_orientation_matches_oracle(ctx):
     d.free()
 
 
+def test_orientation_all_row_classes(ctx):
+    # short rows (combined walk), rows of 129..1024 entries (one warp each) and
+    # rows over 1024 (one block each), int32 and int64 offsets: the DAG must be
+    # the oracle's entry for entry (input rows sorted, compaction keeps order)
+    g = G.disjoint_union([G.star(3000), G.complete(400), G.rmat(12, 16, seed=31), G.star(700)])
+    deg = np.diff(g.row_ptr)
+    assert deg.max() > 1024 and ((deg > 128) & (deg <= 1024)).sum() > 100
+    od = oracle.orient(g)
+    for bits in (32, 64):
+        rp, col = dev(g, bits)
+        d = ctx.orient(g.n, rp, col)
+        dp, dc = d.tensors()
+        assert np.array_equal(dp.cpu().numpy().astype(np.int64), od.dag_ptr)
+        assert np.array_equal(dc.cpu().numpy(), od.dag_col)
+        d.free()
+        assert gpu_count(ctx, g, bits) == oracle.count(g)
+
+
 def test_orientation_unsorted_rows(ctx):
     g = G.shuffle_rows(G.rmat(11, 16, seed=11), 3)
     rp, col = dev(g)
