@@ -101,10 +101,11 @@ typedef struct {
                                     plus one length byte per bucket */
     int32_t warp_min_buckets;    /* a warp-worker table has at least 4*warp_min_buckets slots; power of
                                     two >= 16 (default 16) */
-    int32_t block_threads;       /* threads of a thread-block worker (default 1024) */
-    int32_t block_smem_bytes;    /* shared memory of a thread-block worker (default 200 KiB) */
-    int32_t item_neighbors;      /* out-neighbours of a large vertex per work item, <= block_threads (default 1024) */
-    int32_t chunk;               /* vertices a warp takes per queue pop, 1..32 (Sec. 4.3; paper: 1..7; default 32) */
+    int32_t block_threads;       /* threads of a thread-block worker (default 256) */
+    int32_t block_smem_bytes;    /* shared memory of a thread-block worker (default 50 KiB) */
+    int32_t item_neighbors;      /* out-neighbours of a large vertex per work item, <= block_threads (default 256) */
+    int32_t chunk;               /* most vertices a warp takes per queue pop, 1..32 (Sec. 4.3; paper: 1..7;
+                                    default 32; fewer on short lists, see k_count_pack) */
     int32_t warps_per_block;     /* warps per block of the warp-worker kernel (default 8) */
     int32_t shard_count;         /* workload partition (Sec. 5.1): count only u with */
     int32_t shard_index;         /*   u % shard_count == shard_index (default 1 / 0) */
@@ -267,8 +268,9 @@ tc_status tc_count_batch(tc_ctx* ctx, const tc_csr* gs, int32_t k, uint64_t* cou
 
 /* Autotuner: time the workload gs[0..k) (tc_count for k == 1, tc_count_batch
  * otherwise) under candidate values of warp_max_out_degree (with the table
- * area it needs), warp_min_buckets, chunk, warps_per_block and
- * item_neighbors, one knob at a time, keep the fastest on ctx and return them
+ * area it needs), the thread-block worker shape (block_threads,
+ * block_smem_bytes and item_neighbors together), warp_min_buckets, chunk,
+ * warps_per_block and item_neighbors, one knob at a time, keep the fastest on ctx and return them
  * in *best (may be NULL). gs: device CSRs. cache_path: NULL, or a text file
  * where results are appended per workload signature (graph count, vertex and
  * entry totals in powers of two, offset width) and looked up first. The counts

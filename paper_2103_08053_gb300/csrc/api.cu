@@ -93,9 +93,9 @@ static void fill_defaults(tc_params* p) {
     p->warp_max_out_degree = 128;
     p->warp_area_ints = pack_table_ints(128, 16);
     p->warp_min_buckets = 16;
-    p->block_threads = 1024;
-    p->block_smem_bytes = 200 * 1024;
-    p->item_neighbors = 1024;
+    p->block_threads = 256;
+    p->block_smem_bytes = 50 * 1024;
+    p->item_neighbors = 256;
     p->chunk = 32;
     p->warps_per_block = 8;
     p->shard_count = 1;

@@ -1,5 +1,5 @@
 // tune.cu -- tc_autotune: pick warp-worker threshold, table sizes, queue
-// chunk and block item size for a workload by measurement.
+// chunk, thread-block worker shape and item size for a workload by measurement.
 //
 // Coordinate search: starting from the context's parameters, each knob in
 // turn is set to each of its candidate values (the others held at their best
@@ -66,6 +66,8 @@ bool cache_lookup(const char* path, const std::string& sig, tc_params* p) {
             else if (!strcmp(name, "chunk")) q.chunk = v;
             else if (!strcmp(name, "warps_per_block")) q.warps_per_block = v;
             else if (!strcmp(name, "item_neighbors")) q.item_neighbors = v;
+            else if (!strcmp(name, "block_threads")) q.block_threads = v;
+            else if (!strcmp(name, "block_smem_bytes")) q.block_smem_bytes = v;
         }
         *p = q;
         found = true;  // the last matching line wins
@@ -79,9 +81,9 @@ void cache_store(const char* path, const std::string& sig, const tc_params& p) {
     FILE* f = fopen(path, "a");
     if (!f) return;
     fprintf(f, "%s : warp_max_out_degree=%d warp_area_ints=%d warp_min_buckets=%d chunk=%d warps_per_block=%d "
-               "item_neighbors=%d\n",
+               "item_neighbors=%d block_threads=%d block_smem_bytes=%d\n",
             sig.c_str(), p.warp_max_out_degree, p.warp_area_ints, p.warp_min_buckets, p.chunk, p.warps_per_block,
-            p.item_neighbors);
+            p.item_neighbors, p.block_threads, p.block_smem_bytes);
     fclose(f);
 }
 
@@ -127,6 +129,19 @@ extern "C" tc_status tc_autotune(tc_ctx* ctx, const tc_csr* gs, int32_t k, const
         tc_params p = best;
         p.warp_max_out_degree = tw;
         p.warp_area_ints = pack_table_ints(tw, p.warp_min_buckets);
+        const double ms = trial(ctx, p, gs, k, stream, out, ref);
+        if (ms >= 0 && ms < best_ms) {
+            best_ms = ms;
+            best = p;
+        }
+    }
+    // thread-block workers: threads, shared memory and item size move together
+    const int blocks[][3] = {{1024, 200 * 1024, 1024}, {512, 100 * 1024, 512}, {256, 50 * 1024, 256}};
+    for (const auto& b : blocks) {
+        tc_params p = best;
+        p.block_threads = b[0];
+        p.block_smem_bytes = b[1];
+        p.item_neighbors = b[2];
         const double ms = trial(ctx, p, gs, k, stream, out, ref);
         if (ms >= 0 && ms < best_ms) {
             best_ms = ms;

@@ -368,3 +368,21 @@ def test_build_probe_cycle_split(T):
             shares[ec] = t["build_cycles"] / (t["build_cycles"] + t["probe_cycles"])
             assert c.read_timing()["build_cycles"] == 0      # reading starts a new period
     assert shares[1] > shares[0]
+
+
+def test_host_csr_pinned_and_pageable(ctx):
+    # tc_count_host: pageable arrays are copied first; pinned ones are read by
+    # the orientation's count pass directly, which writes the device copy
+    gs = [G.disjoint_union([G.star(3000), G.complete(300), G.rmat(12, 16, seed=33)]),
+          G.rgg(20_000, 30.0, seed=34), G.empty(9), G.complete(3)]
+    for g in gs:
+        want = oracle.count(g)
+        for bits in (32, 64):
+            rp = np.ascontiguousarray(g.row_ptr.astype(np.int64 if bits == 64 else np.int32))
+            col = np.ascontiguousarray(g.col, dtype=np.int32)
+            assert ctx.count_host(g.n, rp, col) == want
+            rp_pin = torch.from_numpy(rp).pin_memory()
+            col_pin = torch.from_numpy(col).pin_memory()
+            assert col_pin.is_pinned() or g.nnz == 0
+            assert ctx.count_host(g.n, rp_pin.numpy(), col_pin.numpy()) == want
+            assert ctx.count_host(g.n, rp_pin.numpy(), col_pin.numpy()) == want  # reuse the device copy
