@@ -26,10 +26,10 @@ struct DevBuf {
 
 // Scratch of one counting pass.
 struct Workspace {
-    DevBuf deg, kept, partial, dag_ptr, dag_col, warp_list, warp_desc, items, ctr, stats, hubs, kbits;
+    DevBuf deg, kept, partial, dag_ptr, dag_col, warp_list, warp_desc, items, ctr, stats, hubs, kbits, start32;
     void release_all(tc_ctx* ctx) {
         for (DevBuf* b : {&deg, &kept, &partial, &dag_ptr, &dag_col, &warp_list, &warp_desc, &items, &ctr, &stats,
-                          &hubs, &kbits})
+                          &hubs, &kbits, &start32})
             b->release(ctx);
     }
 };

@@ -600,14 +600,17 @@ __device__ __forceinline__ void block_add_total(unsigned long long acc, DevCount
 }
 
 // Bounds of N+(v) for an out-neighbour v (0/0 for no neighbour or a bad id).
-__device__ __forceinline__ void list_bounds(int v, const int32_t* __restrict__ dag_ptr, int n, DevCounters* ctr,
-                                            int& s, int& l) {
+// dag_len: NULL (compact DAG: length from dag_ptr[v + 1]) or the lengths of a
+// row-local DAG.
+__device__ __forceinline__ void list_bounds(int v, const int32_t* __restrict__ dag_ptr,
+                                            const int32_t* __restrict__ dag_len, int n, DevCounters* ctr, int& s,
+                                            int& l) {
     s = 0;
     l = 0;
     if (v >= 0) {
         if (v < n) {
             s = __ldg(dag_ptr + v);
-            l = __ldg(dag_ptr + v + 1) - s;
+            l = dag_len ? __ldg(dag_len + v) : __ldg(dag_ptr + v + 1) - s;
         } else {
             atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
         }
@@ -623,7 +626,7 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
     k_count_pack(const int32_t* __restrict__ dag_ptr, const int32_t* __restrict__ dag_col,
                  const int2* __restrict__ desc, const int32_t* __restrict__ warp_list,
                  unsigned long long* __restrict__ per_vertex, DevCounters* ctr, int n, int area_ints,
-                 int lg_min_buckets, int pop, int quad, int timing) {
+                 int lg_min_buckets, int pop, int quad, int timing, const int32_t* __restrict__ dag_len) {
     extern __shared__ int smem[];
     if (ctr->err) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -729,7 +732,7 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
                 etab = __shfl_sync(FULL, my_tab, o);
                 elg = __shfl_sync(FULL, lgB, o);
                 eslot = o;
-                list_bounds(lane < E ? __ldg(dag_col + bo + lane) : -1, dag_ptr, n, ctr, s, l);
+                list_bounds(lane < E ? __ldg(dag_col + bo + lane) : -1, dag_ptr, dag_len, n, ctr, s, l);
             }
             for (int c0 = 0; c0 < E; c0 += 32) {
                 int ns = 0, nl = 0, ntab = 0, nlg = 0, nslot = 0;
@@ -740,7 +743,7 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
                     nlg = __shfl_sync(FULL, lgB, o);
                     nslot = o;
                     const int e = c0 + 32 + lane;
-                    list_bounds(e < E ? __ldg(dag_col + bo + e) : -1, dag_ptr, n, ctr, ns, nl);
+                    list_bounds(e < E ? __ldg(dag_col + bo + e) : -1, dag_ptr, dag_len, n, ctr, ns, nl);
                 }
                 if (!chained && quad) {
                     hits += vc_pack_quad<PER_VERTEX, HM, PACK_SLOTS>(s, l, etab | (elg << 16) | (eslot << 21), smem, dag_col,
@@ -789,7 +792,8 @@ template <int PIECE, int HM>
 __global__ void __launch_bounds__(1024, 1)
     k_count_block(const int32_t* __restrict__ dag_ptr, const int32_t* __restrict__ dag_col,
                   const int2* __restrict__ items, unsigned long long* __restrict__ per_vertex, DevCounters* ctr,
-                  int n, int table_off, int part_max, int item_nbrs, int quad, int timing) {
+                  int n, int table_off, int part_max, int item_nbrs, int quad, int timing,
+                  const int32_t* __restrict__ dag_len) {
     extern __shared__ int smem[];
     __shared__ int s_item, s_piece;
     __shared__ int s_wsum[32];
@@ -812,11 +816,12 @@ __global__ void __launch_bounds__(1024, 1)
         const int2 item = items[it];
         const int u = item.x;
         const int a = dag_ptr[u];
-        const int k = dag_ptr[u + 1] - a;
+        const int k = dag_len ? dag_len[u] : dag_ptr[u + 1] - a;
         const int nb0 = item.y, cnt = min(k, nb0 + item_nbrs) - nb0;
         // list bounds of the item's out-neighbours, and the block-wide prefix of their lengths
         int ls = 0, ll = 0;
-        if ((int)threadIdx.x < cnt) list_bounds(__ldg(dag_col + a + nb0 + threadIdx.x), dag_ptr, n, ctr, ls, ll);
+        if ((int)threadIdx.x < cnt)
+            list_bounds(__ldg(dag_col + a + nb0 + threadIdx.x), dag_ptr, dag_len, n, ctr, ls, ll);
         // quad path: the prefix counts the quads each list spans
         const int units = (quad && ll > 0) ? ((ls + ll + 3) >> 2) - (ls >> 2) : ll;
         const int wi = warp_incl_scan(units, lane);
@@ -934,7 +939,7 @@ __global__ void __launch_bounds__(256) k_count_edge(const int32_t* __restrict__ 
         uint32_t hu = 0;
         for (int e = 0; e < k; ++e) {
             int s = 0, l = 0;
-            list_bounds(__ldg(dag_col + a + e), dag_ptr, n, ctr, s, l);
+            list_bounds(__ldg(dag_col + a + e), dag_ptr, nullptr, n, ctr, s, l);
             for (int p0 = 0; p0 < k; p0 += part_max) {
                 const long long t0 = timing ? clock64() : 0;
                 const int pk = min(part_max, k - p0);
@@ -1077,7 +1082,7 @@ __global__ void __launch_bounds__(256) k_collision(const int32_t* __restrict__ d
 int pack_smem_bytes(const CountCfg& cfg) { return cfg.warps_per_block * (cfg.warp_area_ints + STAGE_INTS) * 4; }
 
 using PackKernel = void (*)(const int32_t*, const int32_t*, const int2*, const int32_t*, unsigned long long*,
-                            DevCounters*, int, int, int, int, int, int);
+                            DevCounters*, int, int, int, int, int, int, const int32_t*);
 
 PackKernel pack_kernel(bool per_vertex, int hm) {
     if (hm == 1) return per_vertex ? k_count_pack<true, 1> : k_count_pack<false, 1>;
@@ -1085,7 +1090,7 @@ PackKernel pack_kernel(bool per_vertex, int hm) {
 }
 
 using BlockKernel = void (*)(const int32_t*, const int32_t*, const int2*, unsigned long long*, DevCounters*, int,
-                             int, int, int, int, int);
+                             int, int, int, int, int, const int32_t*);
 
 BlockKernel block_kernel(int hm) { return hm == 1 ? k_count_block<BLOCK_PIECE, 1> : k_count_block<BLOCK_PIECE, 0>; }
 
@@ -1164,7 +1169,8 @@ cudaError_t count_kernel_setup(CountCfg& cfg, int num_sms) {
 
 cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t n, const int32_t* warp_list,
                          const int2* warp_desc, const int2* items, unsigned long long* per_vertex,
-                         const CountCfg& cfg, DevCounters* ctr, cudaStream_t st, long long* launches) {
+                         const CountCfg& cfg, DevCounters* ctr, cudaStream_t st, long long* launches,
+                         const int32_t* dag_len) {
     if (cfg.edge_centric) {
         *launches += 1;
         edge_kernel(cfg.hash_mode)<<<cfg.warp_grid, cfg.warps_per_block * 32, pack_smem_bytes(cfg), st>>>(
@@ -1177,11 +1183,11 @@ cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t
     const int quad = (cfg.quad_loads && ((uintptr_t)dag_col & 15) == 0) ? 1 : 0;
     block_kernel(cfg.hash_mode)<<<cfg.block_grid, cfg.block_threads, cfg.block_smem_bytes, st>>>(
         dag_ptr, dag_col, items, per_vertex, ctr, (int)n, table_off, count_block_part_max(cfg), cfg.item_neighbors,
-        quad, cfg.cycle_timing);
+        quad, cfg.cycle_timing, dag_len);
     pack_kernel(per_vertex != nullptr, cfg.hash_mode)<<<cfg.warp_grid, cfg.warps_per_block * 32,
                                                       pack_smem_bytes(cfg), st>>>(
         dag_ptr, dag_col, warp_desc, warp_list, per_vertex, ctr, (int)n, cfg.warp_area_ints,
-        lg2(cfg.warp_min_buckets), cfg.chunk, quad, cfg.cycle_timing);
+        lg2(cfg.warp_min_buckets), cfg.chunk, quad, cfg.cycle_timing, dag_len);
     return cudaGetLastError();
 }
 

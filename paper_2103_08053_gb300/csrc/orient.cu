@@ -45,7 +45,8 @@ __device__ __forceinline__ GraphRef graph_of(int64_t row, const GraphRef& one, c
 
 template <typename Off, bool BATCH>
 __global__ void k_degree(GraphRef one, const GraphRef* __restrict__ gs, int k, int64_t total,
-                         int32_t* __restrict__ deg, int32_t* __restrict__ hubs, DevCounters* ctr) {
+                         int32_t* __restrict__ deg, int32_t* __restrict__ hubs, int32_t* __restrict__ start32,
+                         DevCounters* ctr) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < total; u += stride) {
         const GraphRef G = graph_of<BATCH>(u, one, gs, k);
@@ -61,6 +62,11 @@ __global__ void k_degree(GraphRef one, const GraphRef* __restrict__ gs, int k, i
             }
         }
         deg[u] = (int32_t)d;
+        if (!BATCH && start32 && ul < G.n) {  // row-local DAG: N+(u) starts where N(u) does
+            const Off* rp = static_cast<const Off*>(G.row_ptr);
+            start32[u] = (int32_t)rp[ul];
+            if (u == total - 1) start32[total] = (int32_t)rp[ul + 1];
+        }
         if (d > HUB_DEGREE) hubs[atomicAdd(&ctr->n_hub, 1)] = (int32_t)u;
         else if (d > MID_DEGREE) hubs[total - 1 - atomicAdd(&ctr->n_mid, 1)] = (int32_t)u;  // from the back
     }
@@ -98,7 +104,7 @@ template <typename Off, bool COMPACT, bool BATCH>
 __global__ void __launch_bounds__(ORIENT_THREADS)
     k_orient(GraphRef one, const GraphRef* __restrict__ gs, int k, int64_t total, const int32_t* __restrict__ deg,
              int32_t* __restrict__ kept, const int32_t* __restrict__ dag_ptr, int32_t* __restrict__ dag_col,
-             int64_t dag_cap, unsigned* __restrict__ kbits, DevCounters* ctr) {
+             int64_t dag_cap, unsigned* __restrict__ kbits, int32_t* __restrict__ rdag, DevCounters* ctr) {
     __shared__ long long s_a[ORIENT_WARPS][32];
     __shared__ int s_len[ORIENT_WARPS][32];
     __shared__ int s_rid[ORIENT_WARPS][32];
@@ -220,12 +226,16 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
                 const int lo = max(Pex, bw) - bw, hi = min(P, bw + 32) - bw;
                 const unsigned rowbits =
                     (lst && lo < hi) ? ((hi >= 32 ? FULL : ((1u << hi) - 1u)) & ~((1u << lo) - 1u)) : 0u;
-                if (COMPACT) {
-                    const int next = __shfl_sync(FULL, cnt, o);  // the row's next output position
+                if (COMPACT || rdag) {
+                    // compaction: the row's next position in dag_col; row-local
+                    // count pass: the row's start plus its kept entries so far
+                    const int next = __shfl_sync(FULL, cnt, o) + (COMPACT ? 0 : __shfl_sync(FULL, (int)ca, o));
                     const int first = __shfl_sync(FULL, lo, o);  // the row's first lane in the window
                     if (keep) {
                         const long long pos = (long long)next + __popc(km & lt & ~((1u << first) - 1u));
-                        if (pos < dag_cap)
+                        if (!COMPACT)
+                            rdag[pos] = (int32_t)v;
+                        else if (pos < dag_cap)
                             dag_col[pos] = (int32_t)(vb + v);
                         else
                             atomicOr(&ctr->err, ERRBIT_DAG_OVERFLOW);
@@ -235,6 +245,12 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
             }
         }
         if (!COMPACT && lst) kept[row0 + rid] = cnt;
+        if (!COMPACT && rdag) {  // kept entries of the walk, for the symmetry check
+            int t = cnt;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+            if (lane == 0 && t) atomicAdd(reinterpret_cast<unsigned long long*>(&ctr->m), (unsigned long long)t);
+        }
     }
 }
 
@@ -251,7 +267,8 @@ template <typename Off, bool COMPACT, bool BATCH>
 __global__ void __launch_bounds__(HUB_THREADS)
     k_orient_hub(GraphRef one, const GraphRef* __restrict__ gs, int k, int64_t total, const int32_t* __restrict__ hubs,
                  const int32_t* __restrict__ deg, int32_t* __restrict__ kept, const int32_t* __restrict__ dag_ptr,
-                 int32_t* __restrict__ dag_col, int64_t dag_cap, unsigned* __restrict__ kbits, DevCounters* ctr) {
+                 int32_t* __restrict__ dag_col, int64_t dag_cap, unsigned* __restrict__ kbits,
+                 int32_t* __restrict__ rdag, DevCounters* ctr) {
     __shared__ int s_row, s_carry;
     __shared__ int s_w[HUB_THREADS / 32];
     if (COMPACT && ctr->err) return;
@@ -270,7 +287,12 @@ __global__ void __launch_bounds__(HUB_THREADS)
         const int du = deg[ug];
         if (threadIdx.x == 0) s_carry = 0;
         __syncthreads();
-        long long pos0 = COMPACT ? (long long)dag_ptr[ug] : 0;
+        // output: the compacted DAG, or (row-local count pass) the row itself
+        const bool write = COMPACT || rdag;
+        int32_t* out = COMPACT ? dag_col : rdag;
+        const long long ocap = COMPACT ? dag_cap : 0x7fffffffffffffffLL;
+        const int64_t obase = COMPACT ? G.vbase : 0;
+        long long pos0 = COMPACT ? (long long)dag_ptr[ug] : a;
         int total = 0;
         for (long long t0 = a; t0 < b; t0 += 4LL * HUB_THREADS) {
             const long long e0 = t0 + 4LL * threadIdx.x;
@@ -294,6 +316,7 @@ __global__ void __launch_bounds__(HUB_THREADS)
                 }
                 keepc += kq[q];
             }
+            if (!COMPACT) total += keepc;
             if (!COMPACT) {
                 if (kbits) {
                     // 8 lanes hold 32 consecutive entries as nibbles; the group's
@@ -309,8 +332,7 @@ __global__ void __launch_bounds__(HUB_THREADS)
                         if (sh) atomicOr(kbits + (e0 >> 5) + 1, word >> (32 - sh));
                     }
                 }
-                total += keepc;
-                continue;
+                if (!write) continue;
             }
             // exclusive block scan of keepc
             int inc = keepc;
@@ -336,8 +358,8 @@ __global__ void __launch_bounds__(HUB_THREADS)
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 if (kq[q]) {
-                    if (p < dag_cap)
-                        dag_col[p] = (int32_t)(G.vbase + v[q]);
+                    if (p < ocap)
+                        out[p] = (int32_t)(obase + v[q]);
                     else
                         atomicOr(&ctr->err, ERRBIT_DAG_OVERFLOW);
                     ++p;
@@ -356,6 +378,7 @@ __global__ void __launch_bounds__(HUB_THREADS)
                 int t = 0;
                 for (int i = 0; i < nw; ++i) t += s_w[i];
                 kept[ug] = t;
+                if (rdag && t) atomicAdd(reinterpret_cast<unsigned long long*>(&ctr->m), (unsigned long long)t);
             }
         }
         __syncthreads();
@@ -407,21 +430,30 @@ __global__ void __launch_bounds__(HUB_THREADS)
                     if (km1 >> (32 - sh)) atomicOr(wd + 2, km1 >> (32 - sh));
                 }
             }
-            if (COMPACT) {
-                const long long p0 = (long long)rc + __popc(km0 & lt);
-                const long long p1 = (long long)rc + __popc(km0) + __popc(km1 & lt);
-                if (k0) {
-                    if (p0 < dag_cap) dag_col[p0] = (int32_t)(G.vbase + v0);
-                    else atomicOr(&ctr->err, ERRBIT_DAG_OVERFLOW);
-                }
-                if (k1) {
-                    if (p1 < dag_cap) dag_col[p1] = (int32_t)(G.vbase + v1);
-                    else atomicOr(&ctr->err, ERRBIT_DAG_OVERFLOW);
+            if (COMPACT || rdag) {
+                const long long rb = COMPACT ? (long long)rc : ra + rc;  // next position of the row's output
+                const long long p0 = rb + __popc(km0 & lt);
+                const long long p1 = rb + __popc(km0) + __popc(km1 & lt);
+                if (!COMPACT) {
+                    if (k0) rdag[p0] = v0;
+                    if (k1) rdag[p1] = v1;
+                } else {
+                    if (k0) {
+                        if (p0 < dag_cap) dag_col[p0] = (int32_t)(G.vbase + v0);
+                        else atomicOr(&ctr->err, ERRBIT_DAG_OVERFLOW);
+                    }
+                    if (k1) {
+                        if (p1 < dag_cap) dag_col[p1] = (int32_t)(G.vbase + v1);
+                        else atomicOr(&ctr->err, ERRBIT_DAG_OVERFLOW);
+                    }
                 }
             }
             rc += __popc(km0) + __popc(km1);
         }
-        if (!COMPACT && lane == 0) kept[ug] = rc;
+        if (!COMPACT && lane == 0) {
+            kept[ug] = rc;
+            if (rdag && rc) atomicAdd(reinterpret_cast<unsigned long long*>(&ctr->m), (unsigned long long)rc);
+        }
     }
 }
 
@@ -527,10 +559,15 @@ __global__ void __launch_bounds__(SCAN_THREADS)
 
 // ---- binning ----------------------------------------------------------------
 
-__global__ void k_bin(const int32_t* __restrict__ dag_ptr, int64_t n, int warp_max, int item_nbrs, int shard_count,
-                      int shard_index, int32_t* __restrict__ warp_list, int2* __restrict__ warp_desc,
-                      int2* __restrict__ items, int64_t item_cap, DevCounters* ctr) {
+__global__ void k_bin(const int32_t* __restrict__ dag_ptr, const int32_t* __restrict__ dag_len, int64_t n,
+                      int warp_max, int item_nbrs, int shard_count, int shard_index, int32_t* __restrict__ warp_list,
+                      int2* __restrict__ warp_desc, int2* __restrict__ items, int64_t item_cap, long long max_m,
+                      DevCounters* ctr) {
     if (ctr->err) return;
+    if (max_m >= 0 && ctr->m > max_m) {  // more kept entries than an undirected CSR can give
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&ctr->err, ERRBIT_DAG_OVERFLOW);
+        return;
+    }
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
@@ -538,7 +575,7 @@ __global__ void k_bin(const int32_t* __restrict__ dag_ptr, int64_t n, int warp_m
         int d = 0, a = 0;
         if (u < n && (shard_count <= 1 || (int)(u % shard_count) == shard_index)) {
             a = dag_ptr[u];
-            d = dag_ptr[u + 1] - a;
+            d = dag_len ? dag_len[u] : dag_ptr[u + 1] - a;
         }
         const bool is_warp = d >= 2 && d <= warp_max;
         const unsigned wm = __ballot_sync(FULL, is_warp);
@@ -569,14 +606,15 @@ __global__ void k_bin(const int32_t* __restrict__ dag_ptr, int64_t n, int warp_m
 template <typename Off, bool BATCH>
 cudaError_t orient_t(const GraphRef& one, const GraphRef* gs, int k, int64_t total, int32_t* deg, int32_t* kept,
                      long long* partial, int32_t* dag_ptr, int32_t* dag_col, int64_t dag_cap, int32_t* hubs,
-                     unsigned* kbits, int64_t kbits_words, DevCounters* ctr, int num_sms, cudaStream_t st,
-                     long long* launches) {
+                     unsigned* kbits, int64_t kbits_words, int32_t* start32, int32_t* rdag, DevCounters* ctr,
+                     int num_sms, cudaStream_t st, long long* launches) {
     if (total <= 0) return cudaSuccess;
+    if (rdag) kbits = nullptr;  // the row-local DAG needs no compaction pass
     if (kbits) {
         const cudaError_t e = cudaMemsetAsync(kbits, 0, (size_t)kbits_words * 4, st);
         if (e != cudaSuccess) return e;
     }
-    *launches += 8;
+    *launches += rdag ? 3 : 8;
     const int hg = num_sms * 2;
     const int64_t groups = (total + 31) / 32;
     int og = (int)((groups + ORIENT_WARPS - 1) / ORIENT_WARPS);
@@ -584,19 +622,20 @@ cudaError_t orient_t(const GraphRef& one, const GraphRef* gs, int k, int64_t tot
     if (og > og_cap) og = og_cap;
     int dg = (int)((total + 255) / 256);
     if (dg > num_sms * 16) dg = num_sms * 16;
-    k_degree<Off, BATCH><<<dg, 256, 0, st>>>(one, gs, k, total, deg, hubs, ctr);
+    k_degree<Off, BATCH><<<dg, 256, 0, st>>>(one, gs, k, total, deg, hubs, start32, ctr);
     k_orient<Off, false, BATCH><<<og, ORIENT_THREADS, 0, st>>>(one, gs, k, total, deg, kept, nullptr, nullptr, 0,
-                                                                kbits, ctr);
+                                                                kbits, rdag, ctr);
     k_orient_hub<Off, false, BATCH><<<hg, HUB_THREADS, 0, st>>>(one, gs, k, total, hubs, deg, kept, nullptr, nullptr, 0,
-                                                                 kbits, ctr);
+                                                                 kbits, rdag, ctr);
+    if (rdag) return cudaGetLastError();  // row-local DAG: start32 / kept / rdag are the DAG
     const int nb = scan_blocks(total);
     k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(kept, total, partial);
     k_scan_top<<<1, SCAN_TOP_THREADS, 0, st>>>(partial, nb, dag_ptr, total, ctr);
     k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(kept, total, partial, dag_ptr);
     k_orient<Off, true, BATCH><<<og, ORIENT_THREADS, 0, st>>>(one, gs, k, total, deg, nullptr, dag_ptr, dag_col,
-                                                               dag_cap, kbits, ctr);
+                                                               dag_cap, kbits, nullptr, ctr);
     k_orient_hub<Off, true, BATCH><<<hg, HUB_THREADS, 0, st>>>(one, gs, k, total, hubs, deg, nullptr, dag_ptr, dag_col,
-                                                                dag_cap, kbits, ctr);
+                                                                dag_cap, kbits, nullptr, ctr);
     return cudaGetLastError();
 }
 
@@ -607,14 +646,14 @@ int scan_blocks(int64_t n) { return (int)((n + SCAN_TILE - 1) / SCAN_TILE); }
 cudaError_t launch_orient(const void* row_ptr, int offset_bits, const int32_t* col, int64_t n, int64_t nnz,
                           int32_t* deg, int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
                           int64_t dag_cap, int32_t* hubs, unsigned* kbits, DevCounters* ctr, int num_sms,
-                          cudaStream_t st, long long* launches) {
+                          cudaStream_t st, long long* launches, int32_t* start32, int32_t* rdag) {
     const GraphRef one{row_ptr, col, n, nnz, 0};
     const int64_t words = keep_bits_words(nnz);
     if (offset_bits == 64)
         return orient_t<long long, false>(one, nullptr, 1, n, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs,
-                                          kbits, words, ctr, num_sms, st, launches);
+                                          kbits, words, start32, rdag, ctr, num_sms, st, launches);
     return orient_t<int32_t, false>(one, nullptr, 1, n, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs, kbits,
-                                    words, ctr, num_sms, st, launches);
+                                    words, start32, rdag, ctr, num_sms, st, launches);
 }
 
 cudaError_t launch_orient_batch(const GraphRef* graphs, int k, int offset_bits, int64_t total, int32_t* deg,
@@ -624,20 +663,20 @@ cudaError_t launch_orient_batch(const GraphRef* graphs, int k, int offset_bits, 
     const GraphRef none{nullptr, nullptr, 0, 0, 0};
     if (offset_bits == 64)
         return orient_t<long long, true>(none, graphs, k, total, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs,
-                                         nullptr, 0, ctr, num_sms, st, launches);
+                                         nullptr, 0, nullptr, nullptr, ctr, num_sms, st, launches);
     return orient_t<int32_t, true>(none, graphs, k, total, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs,
-                                   nullptr, 0, ctr, num_sms, st, launches);
+                                   nullptr, 0, nullptr, nullptr, ctr, num_sms, st, launches);
 }
 
 cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* warp_desc,
                        int2* items, int64_t item_cap, DevCounters* ctr, int num_sms, cudaStream_t st,
-                       long long* launches) {
+                       long long* launches, const int32_t* dag_len, long long max_m) {
     if (n <= 0) return cudaSuccess;
     *launches += 1;
     int g = (int)((n + 255) / 256);
     if (g > num_sms * 16) g = num_sms * 16;
-    k_bin<<<g, 256, 0, st>>>(dag_ptr, n, cfg.warp_max_out_degree, cfg.item_neighbors, cfg.shard_count,
-                             cfg.shard_index, warp_list, warp_desc, items, item_cap, ctr);
+    k_bin<<<g, 256, 0, st>>>(dag_ptr, dag_len, n, cfg.warp_max_out_degree, cfg.item_neighbors, cfg.shard_count,
+                             cfg.shard_index, warp_list, warp_desc, items, item_cap, max_m, ctr);
     return cudaGetLastError();
 }
 

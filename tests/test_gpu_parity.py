@@ -348,9 +348,15 @@ def test_phase_timing_and_launch_count(T):
         rp, col = dev(g)
         l0 = c.kernel_launches()
         assert c.count(g.n, rp, col) == oracle.count(g)
-        assert c.kernel_launches() - l0 == 12   # 8 orientation + bin + 2 counting + finish
+        # row-local DAG: degree + 2 orientation count kernels, bin, 2 counting, finish
+        assert c.kernel_launches() - l0 == 7
+        d = c.orient(g.n, rp, col)              # a compact DAG: 8 orientation kernels
+        l1 = c.kernel_launches()
+        assert c.count_dag(d) == oracle.count(g)
+        assert c.kernel_launches() - l1 == 3     # bin + 2 counting
+        d.free()
         t = c.read_timing()
-        assert t["calls"] == 1 and t["orient_ms"] > 0 and t["count_ms"] > 0
+        assert t["calls"] == 2 and t["orient_ms"] > 0 and t["count_ms"] > 0
         assert c.read_timing()["calls"] == 0
 
 
