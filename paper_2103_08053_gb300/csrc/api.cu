@@ -264,11 +264,11 @@ static tc_status enqueue_orient(tc_ctx* ctx, Workspace& ws, const tc_csr* g, int
 }
 
 // Binning + counting; tm (may be null) gets events 2 (after binning) and 3.
-// dag_len / max_m: a row-local DAG's lengths and the most kept entries the
-// input allows (nullptr / -1 for a compact DAG).
+// dag_bnd / max_m: a row-local DAG's (start, length) pairs and the most kept
+// entries the input allows (nullptr / -1 for a compact DAG).
 static tc_status enqueue_count(tc_ctx* ctx, Workspace& ws, const int32_t* dag_ptr, const int32_t* dag_col,
                                int64_t n, uint64_t* per_vertex, cudaStream_t st, TimedCall* tm,
-                               const int32_t* dag_len = nullptr, long long max_m = -1) {
+                               const int2* dag_bnd = nullptr, long long max_m = -1) {
     DevCounters* ctr = (DevCounters*)ws.ctr.p;
     cudaError_t e = cudaSuccess;
     long long nl = 0;
@@ -276,12 +276,12 @@ static tc_status enqueue_count(tc_ctx* ctx, Workspace& ws, const int32_t* dag_pt
     if (e == cudaSuccess && n > 0) {
         const int64_t m_cap = ws.items.bytes / sizeof(int2);
         e = launch_bin(dag_ptr, n, ctx->cfg, (int32_t*)ws.warp_list.p, (int2*)ws.warp_desc.p, (int2*)ws.items.p,
-                       m_cap, ctr, ctx->num_sms, st, &nl, dag_len, max_m);
+                       m_cap, ctr, ctx->num_sms, st, &nl, dag_bnd, max_m);
         timing_mark(tm, 2, st);
         if (e == cudaSuccess)
             e = launch_count(dag_ptr, dag_col, n, (const int32_t*)ws.warp_list.p, (const int2*)ws.warp_desc.p,
                              (const int2*)ws.items.p, (unsigned long long*)per_vertex, ctx->cfg, ctr, st, &nl,
-                             dag_len);
+                             dag_bnd);
     } else {
         timing_mark(tm, 2, st);
     }
@@ -500,7 +500,7 @@ tc_status tc_count_async(tc_ctx* ctx, const tc_csr* g, uint64_t* count_device, i
     // no compaction) whenever the offsets fit int32; else the compact DAG
     const bool row_local = g->nnz < 0x7fffffffLL && !ctx->cfg.edge_centric;
     if (row_local) {
-        if ((s = ws.start32.ensure(ctx, (size_t)(g->n + 1) * 4, st))) return s;
+        if ((s = ws.bnd.ensure(ctx, (size_t)(g->n + 1) * 8, st))) return s;
         if ((s = ws.dag_col.ensure(ctx, (size_t)(g->nnz + 1) * 4, st))) return s;
     } else if ((s = ws.dag_col.ensure(ctx, (size_t)(g->nnz / 2 + 1) * 4, st))) {
         return s;
@@ -514,14 +514,14 @@ tc_status tc_count_async(tc_ctx* ctx, const tc_csr* g, uint64_t* count_device, i
             cudaError_t e = launch_orient(g->row_ptr, g->offset_bits, g->col, g->n, g->nnz, (int32_t*)ws.deg.p,
                                           (int32_t*)ws.kept.p, nullptr, nullptr, nullptr, 0, (int32_t*)ws.hubs.p,
                                           nullptr, (DevCounters*)ws.ctr.p, ctx->num_sms, st, &nl,
-                                          (int32_t*)ws.start32.p, (int32_t*)ws.dag_col.p);
+                                          (int2*)ws.bnd.p, (int32_t*)ws.dag_col.p);
             ctx->launches += nl;
             s = cuda_status(ctx, e, "orientation kernels");
         }
         timing_mark(tm, 1, st);
         if (!s)
-            s = enqueue_count(ctx, ws, (int32_t*)ws.start32.p, (int32_t*)ws.dag_col.p, g->n, nullptr, st, tm,
-                              (int32_t*)ws.kept.p, g->nnz / 2);
+            s = enqueue_count(ctx, ws, nullptr, (int32_t*)ws.dag_col.p, g->n, nullptr, st, tm, (int2*)ws.bnd.p,
+                              g->nnz / 2);
     } else {
         if (!s) s = enqueue_orient(ctx, ws, g, (int32_t*)ws.dag_ptr.p, (int32_t*)ws.dag_col.p, g->nnz / 2 + 1, st);
         timing_mark(tm, 1, st);

@@ -26,10 +26,10 @@ struct DevBuf {
 
 // Scratch of one counting pass.
 struct Workspace {
-    DevBuf deg, kept, partial, dag_ptr, dag_col, warp_list, warp_desc, items, ctr, stats, hubs, kbits, start32;
+    DevBuf deg, kept, partial, dag_ptr, dag_col, warp_list, warp_desc, items, ctr, stats, hubs, kbits, bnd;
     void release_all(tc_ctx* ctx) {
         for (DevBuf* b : {&deg, &kept, &partial, &dag_ptr, &dag_col, &warp_list, &warp_desc, &items, &ctr, &stats,
-                          &hubs, &kbits, &start32})
+                          &hubs, &kbits, &bnd})
             b->release(ctx);
     }
 };

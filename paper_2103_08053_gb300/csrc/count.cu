@@ -600,17 +600,23 @@ __device__ __forceinline__ void block_add_total(unsigned long long acc, DevCount
 }
 
 // Bounds of N+(v) for an out-neighbour v (0/0 for no neighbour or a bad id).
-// dag_len: NULL (compact DAG: length from dag_ptr[v + 1]) or the lengths of a
-// row-local DAG.
+// dag_bnd: NULL (compact DAG: dag_ptr[v], dag_ptr[v + 1]) or the (start,
+// length) pairs of a row-local DAG (one 8-byte load).
 __device__ __forceinline__ void list_bounds(int v, const int32_t* __restrict__ dag_ptr,
-                                            const int32_t* __restrict__ dag_len, int n, DevCounters* ctr, int& s,
+                                            const int2* __restrict__ dag_bnd, int n, DevCounters* ctr, int& s,
                                             int& l) {
     s = 0;
     l = 0;
     if (v >= 0) {
         if (v < n) {
-            s = __ldg(dag_ptr + v);
-            l = dag_len ? __ldg(dag_len + v) : __ldg(dag_ptr + v + 1) - s;
+            if (dag_bnd) {
+                const int2 b = __ldg(dag_bnd + v);
+                s = b.x;
+                l = b.y;
+            } else {
+                s = __ldg(dag_ptr + v);
+                l = __ldg(dag_ptr + v + 1) - s;
+            }
         } else {
             atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
         }
@@ -626,11 +632,11 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
     k_count_pack(const int32_t* __restrict__ dag_ptr, const int32_t* __restrict__ dag_col,
                  const int2* __restrict__ desc, const int32_t* __restrict__ warp_list,
                  unsigned long long* __restrict__ per_vertex, DevCounters* ctr, int n, int area_ints,
-                 int lg_min_buckets, int pop, int quad, int timing, const int32_t* __restrict__ dag_len) {
+                 int lg_min_buckets, int pop, int quad, int timing, const int2* __restrict__ dag_bnd) {
     extern __shared__ int smem[];
     if (ctr->err) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int m = quad ? __ldg(dag_ptr + n) : 0;  // readable dag_col entries (quad path)
+    const int m = quad ? (dag_bnd ? dag_bnd[n].x : __ldg(dag_ptr + n)) : 0;  // readable dag_col entries
     long long cyc_b = 0, cyc_p = 0;               // build / probe cycles (timing only)
     const unsigned le = lanemask_le(lane);
     const int area = w * (area_ints + STAGE_INTS);  // int offset of this warp's area in smem
@@ -732,7 +738,7 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
                 etab = __shfl_sync(FULL, my_tab, o);
                 elg = __shfl_sync(FULL, lgB, o);
                 eslot = o;
-                list_bounds(lane < E ? __ldg(dag_col + bo + lane) : -1, dag_ptr, dag_len, n, ctr, s, l);
+                list_bounds(lane < E ? __ldg(dag_col + bo + lane) : -1, dag_ptr, dag_bnd, n, ctr, s, l);
             }
             for (int c0 = 0; c0 < E; c0 += 32) {
                 int ns = 0, nl = 0, ntab = 0, nlg = 0, nslot = 0;
@@ -743,7 +749,7 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
                     nlg = __shfl_sync(FULL, lgB, o);
                     nslot = o;
                     const int e = c0 + 32 + lane;
-                    list_bounds(e < E ? __ldg(dag_col + bo + e) : -1, dag_ptr, dag_len, n, ctr, ns, nl);
+                    list_bounds(e < E ? __ldg(dag_col + bo + e) : -1, dag_ptr, dag_bnd, n, ctr, ns, nl);
                 }
                 if (!chained && quad) {
                     hits += vc_pack_quad<PER_VERTEX, HM, PACK_SLOTS>(s, l, etab | (elg << 16) | (eslot << 21), smem, dag_col,
@@ -793,14 +799,14 @@ __global__ void __launch_bounds__(1024, 1)
     k_count_block(const int32_t* __restrict__ dag_ptr, const int32_t* __restrict__ dag_col,
                   const int2* __restrict__ items, unsigned long long* __restrict__ per_vertex, DevCounters* ctr,
                   int n, int table_off, int part_max, int item_nbrs, int quad, int timing,
-                  const int32_t* __restrict__ dag_len) {
+                  const int2* __restrict__ dag_bnd) {
     extern __shared__ int smem[];
     __shared__ int s_item, s_piece;
     __shared__ int s_wsum[32];
     if (ctr->err) return;
     long long cyc_b = 0, cyc_p = 0;  // build / probe cycles of this warp (timing only)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int m = quad ? __ldg(dag_ptr + n) : 0;  // readable dag_col entries (quad path)
+    const int m = quad ? (dag_bnd ? dag_bnd[n].x : __ldg(dag_ptr + n)) : 0;  // readable dag_col entries
     int* stage = smem + w * BLOCK_STAGE_INTS;
     int* S = smem + nw * BLOCK_STAGE_INTS;
     int* E = S + item_nbrs;
@@ -815,13 +821,13 @@ __global__ void __launch_bounds__(1024, 1)
         if (it >= nitems) break;
         const int2 item = items[it];
         const int u = item.x;
-        const int a = dag_ptr[u];
-        const int k = dag_len ? dag_len[u] : dag_ptr[u + 1] - a;
+        const int a = dag_bnd ? dag_bnd[u].x : dag_ptr[u];
+        const int k = dag_bnd ? dag_bnd[u].y : dag_ptr[u + 1] - a;
         const int nb0 = item.y, cnt = min(k, nb0 + item_nbrs) - nb0;
         // list bounds of the item's out-neighbours, and the block-wide prefix of their lengths
         int ls = 0, ll = 0;
         if ((int)threadIdx.x < cnt)
-            list_bounds(__ldg(dag_col + a + nb0 + threadIdx.x), dag_ptr, dag_len, n, ctr, ls, ll);
+            list_bounds(__ldg(dag_col + a + nb0 + threadIdx.x), dag_ptr, dag_bnd, n, ctr, ls, ll);
         // quad path: the prefix counts the quads each list spans
         const int units = (quad && ll > 0) ? ((ls + ll + 3) >> 2) - (ls >> 2) : ll;
         const int wi = warp_incl_scan(units, lane);
@@ -1082,7 +1088,7 @@ __global__ void __launch_bounds__(256) k_collision(const int32_t* __restrict__ d
 int pack_smem_bytes(const CountCfg& cfg) { return cfg.warps_per_block * (cfg.warp_area_ints + STAGE_INTS) * 4; }
 
 using PackKernel = void (*)(const int32_t*, const int32_t*, const int2*, const int32_t*, unsigned long long*,
-                            DevCounters*, int, int, int, int, int, int, const int32_t*);
+                            DevCounters*, int, int, int, int, int, int, const int2*);
 
 PackKernel pack_kernel(bool per_vertex, int hm) {
     if (hm == 1) return per_vertex ? k_count_pack<true, 1> : k_count_pack<false, 1>;
@@ -1090,7 +1096,7 @@ PackKernel pack_kernel(bool per_vertex, int hm) {
 }
 
 using BlockKernel = void (*)(const int32_t*, const int32_t*, const int2*, unsigned long long*, DevCounters*, int,
-                             int, int, int, int, int, const int32_t*);
+                             int, int, int, int, int, const int2*);
 
 BlockKernel block_kernel(int hm) { return hm == 1 ? k_count_block<BLOCK_PIECE, 1> : k_count_block<BLOCK_PIECE, 0>; }
 
@@ -1170,7 +1176,7 @@ cudaError_t count_kernel_setup(CountCfg& cfg, int num_sms) {
 cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t n, const int32_t* warp_list,
                          const int2* warp_desc, const int2* items, unsigned long long* per_vertex,
                          const CountCfg& cfg, DevCounters* ctr, cudaStream_t st, long long* launches,
-                         const int32_t* dag_len) {
+                         const int2* dag_bnd) {
     if (cfg.edge_centric) {
         *launches += 1;
         edge_kernel(cfg.hash_mode)<<<cfg.warp_grid, cfg.warps_per_block * 32, pack_smem_bytes(cfg), st>>>(
@@ -1183,11 +1189,11 @@ cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t
     const int quad = (cfg.quad_loads && ((uintptr_t)dag_col & 15) == 0) ? 1 : 0;
     block_kernel(cfg.hash_mode)<<<cfg.block_grid, cfg.block_threads, cfg.block_smem_bytes, st>>>(
         dag_ptr, dag_col, items, per_vertex, ctr, (int)n, table_off, count_block_part_max(cfg), cfg.item_neighbors,
-        quad, cfg.cycle_timing, dag_len);
+        quad, cfg.cycle_timing, dag_bnd);
     pack_kernel(per_vertex != nullptr, cfg.hash_mode)<<<cfg.warp_grid, cfg.warps_per_block * 32,
                                                       pack_smem_bytes(cfg), st>>>(
         dag_ptr, dag_col, warp_desc, warp_list, per_vertex, ctr, (int)n, cfg.warp_area_ints,
-        lg2(cfg.warp_min_buckets), cfg.chunk, quad, cfg.cycle_timing, dag_len);
+        lg2(cfg.warp_min_buckets), cfg.chunk, quad, cfg.cycle_timing, dag_bnd);
     return cudaGetLastError();
 }
 

@@ -45,7 +45,7 @@ __device__ __forceinline__ GraphRef graph_of(int64_t row, const GraphRef& one, c
 
 template <typename Off, bool BATCH>
 __global__ void k_degree(GraphRef one, const GraphRef* __restrict__ gs, int k, int64_t total,
-                         int32_t* __restrict__ deg, int32_t* __restrict__ hubs, int32_t* __restrict__ start32,
+                         int32_t* __restrict__ deg, int32_t* __restrict__ hubs, int2* __restrict__ bnd,
                          DevCounters* ctr) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < total; u += stride) {
@@ -62,11 +62,8 @@ __global__ void k_degree(GraphRef one, const GraphRef* __restrict__ gs, int k, i
             }
         }
         deg[u] = (int32_t)d;
-        if (!BATCH && start32 && ul < G.n) {  // row-local DAG: N+(u) starts where N(u) does
-            const Off* rp = static_cast<const Off*>(G.row_ptr);
-            start32[u] = (int32_t)rp[ul];
-            if (u == total - 1) start32[total] = (int32_t)rp[ul + 1];
-        }
+        if (!BATCH && bnd && u == total - 1)  // row-local DAG: entries readable past the last list
+            bnd[total] = make_int2((int32_t)static_cast<const Off*>(G.row_ptr)[ul + 1], 0);
         if (d > HUB_DEGREE) hubs[atomicAdd(&ctr->n_hub, 1)] = (int32_t)u;
         else if (d > MID_DEGREE) hubs[total - 1 - atomicAdd(&ctr->n_mid, 1)] = (int32_t)u;  // from the back
     }
@@ -104,7 +101,8 @@ template <typename Off, bool COMPACT, bool BATCH>
 __global__ void __launch_bounds__(ORIENT_THREADS)
     k_orient(GraphRef one, const GraphRef* __restrict__ gs, int k, int64_t total, const int32_t* __restrict__ deg,
              int32_t* __restrict__ kept, const int32_t* __restrict__ dag_ptr, int32_t* __restrict__ dag_col,
-             int64_t dag_cap, unsigned* __restrict__ kbits, int32_t* __restrict__ rdag, DevCounters* ctr) {
+             int64_t dag_cap, unsigned* __restrict__ kbits, int32_t* __restrict__ rdag, int2* __restrict__ bnd,
+             DevCounters* ctr) {
     __shared__ long long s_a[ORIENT_WARPS][32];
     __shared__ int s_len[ORIENT_WARPS][32];
     __shared__ int s_rid[ORIENT_WARPS][32];
@@ -138,7 +136,10 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
         const long long len = nx - a;
         // rows walked here: non-empty and not hubs (the hub kernel takes those)
         const bool walk = lane < nr && len > 0 && len <= MID_DEGREE;
-        if (!COMPACT && (BATCH || lane < nr) && !walk) kept[row0 + lane] = 0;  // hub rows: rewritten later
+        if (!COMPACT && (BATCH || lane < nr) && !walk) {  // mid and hub rows: rewritten later
+            if (bnd) bnd[row0 + lane] = make_int2((int)a, 0);
+            else kept[row0 + lane] = 0;
+        }
         const unsigned wm = __ballot_sync(FULL, walk);
         if (wm == 0) continue;
         const bool hubless = __ballot_sync(FULL, lane < nr && len > MID_DEGREE) == 0;
@@ -244,7 +245,10 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
                 cnt += __popc(km & rowbits);
             }
         }
-        if (!COMPACT && lst) kept[row0 + rid] = cnt;
+        if (!COMPACT && lst) {
+            if (bnd) bnd[row0 + rid] = make_int2((int)ca, cnt);  // row-local DAG: (start, d+)
+            else kept[row0 + rid] = cnt;
+        }
         if (!COMPACT && rdag) {  // kept entries of the walk, for the symmetry check
             int t = cnt;
 #pragma unroll
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(HUB_THREADS)
     k_orient_hub(GraphRef one, const GraphRef* __restrict__ gs, int k, int64_t total, const int32_t* __restrict__ hubs,
                  const int32_t* __restrict__ deg, int32_t* __restrict__ kept, const int32_t* __restrict__ dag_ptr,
                  int32_t* __restrict__ dag_col, int64_t dag_cap, unsigned* __restrict__ kbits,
-                 int32_t* __restrict__ rdag, DevCounters* ctr) {
+                 int32_t* __restrict__ rdag, int2* __restrict__ bnd, DevCounters* ctr) {
     __shared__ int s_row, s_carry;
     __shared__ int s_w[HUB_THREADS / 32];
     if (COMPACT && ctr->err) return;
@@ -377,7 +381,8 @@ __global__ void __launch_bounds__(HUB_THREADS)
             if (threadIdx.x == 0) {
                 int t = 0;
                 for (int i = 0; i < nw; ++i) t += s_w[i];
-                kept[ug] = t;
+                if (bnd) bnd[ug] = make_int2((int)a, t);
+                else kept[ug] = t;
                 if (rdag && t) atomicAdd(reinterpret_cast<unsigned long long*>(&ctr->m), (unsigned long long)t);
             }
         }
@@ -451,7 +456,8 @@ __global__ void __launch_bounds__(HUB_THREADS)
             rc += __popc(km0) + __popc(km1);
         }
         if (!COMPACT && lane == 0) {
-            kept[ug] = rc;
+            if (bnd) bnd[ug] = make_int2((int)ra, rc);
+            else kept[ug] = rc;
             if (rdag && rc) atomicAdd(reinterpret_cast<unsigned long long*>(&ctr->m), (unsigned long long)rc);
         }
     }
@@ -559,7 +565,7 @@ __global__ void __launch_bounds__(SCAN_THREADS)
 
 // ---- binning ----------------------------------------------------------------
 
-__global__ void k_bin(const int32_t* __restrict__ dag_ptr, const int32_t* __restrict__ dag_len, int64_t n,
+__global__ void k_bin(const int32_t* __restrict__ dag_ptr, const int2* __restrict__ dag_bnd, int64_t n,
                       int warp_max, int item_nbrs, int shard_count, int shard_index, int32_t* __restrict__ warp_list,
                       int2* __restrict__ warp_desc, int2* __restrict__ items, int64_t item_cap, long long max_m,
                       DevCounters* ctr) {
@@ -574,8 +580,14 @@ __global__ void k_bin(const int32_t* __restrict__ dag_ptr, const int32_t* __rest
         const int64_t u = base + threadIdx.x;
         int d = 0, a = 0;
         if (u < n && (shard_count <= 1 || (int)(u % shard_count) == shard_index)) {
-            a = dag_ptr[u];
-            d = dag_len ? dag_len[u] : dag_ptr[u + 1] - a;
+            if (dag_bnd) {
+                const int2 b = dag_bnd[u];
+                a = b.x;
+                d = b.y;
+            } else {
+                a = dag_ptr[u];
+                d = dag_ptr[u + 1] - a;
+            }
         }
         const bool is_warp = d >= 2 && d <= warp_max;
         const unsigned wm = __ballot_sync(FULL, is_warp);
@@ -606,7 +618,7 @@ __global__ void k_bin(const int32_t* __restrict__ dag_ptr, const int32_t* __rest
 template <typename Off, bool BATCH>
 cudaError_t orient_t(const GraphRef& one, const GraphRef* gs, int k, int64_t total, int32_t* deg, int32_t* kept,
                      long long* partial, int32_t* dag_ptr, int32_t* dag_col, int64_t dag_cap, int32_t* hubs,
-                     unsigned* kbits, int64_t kbits_words, int32_t* start32, int32_t* rdag, DevCounters* ctr,
+                     unsigned* kbits, int64_t kbits_words, int2* bnd, int32_t* rdag, DevCounters* ctr,
                      int num_sms, cudaStream_t st, long long* launches) {
     if (total <= 0) return cudaSuccess;
     if (rdag) kbits = nullptr;  // the row-local DAG needs no compaction pass
@@ -622,20 +634,20 @@ cudaError_t orient_t(const GraphRef& one, const GraphRef* gs, int k, int64_t tot
     if (og > og_cap) og = og_cap;
     int dg = (int)((total + 255) / 256);
     if (dg > num_sms * 16) dg = num_sms * 16;
-    k_degree<Off, BATCH><<<dg, 256, 0, st>>>(one, gs, k, total, deg, hubs, start32, ctr);
+    k_degree<Off, BATCH><<<dg, 256, 0, st>>>(one, gs, k, total, deg, hubs, bnd, ctr);
     k_orient<Off, false, BATCH><<<og, ORIENT_THREADS, 0, st>>>(one, gs, k, total, deg, kept, nullptr, nullptr, 0,
-                                                                kbits, rdag, ctr);
+                                                                kbits, rdag, bnd, ctr);
     k_orient_hub<Off, false, BATCH><<<hg, HUB_THREADS, 0, st>>>(one, gs, k, total, hubs, deg, kept, nullptr, nullptr, 0,
-                                                                 kbits, rdag, ctr);
-    if (rdag) return cudaGetLastError();  // row-local DAG: start32 / kept / rdag are the DAG
+                                                                 kbits, rdag, bnd, ctr);
+    if (rdag) return cudaGetLastError();  // row-local DAG: bnd and rdag are the DAG
     const int nb = scan_blocks(total);
     k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(kept, total, partial);
     k_scan_top<<<1, SCAN_TOP_THREADS, 0, st>>>(partial, nb, dag_ptr, total, ctr);
     k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(kept, total, partial, dag_ptr);
     k_orient<Off, true, BATCH><<<og, ORIENT_THREADS, 0, st>>>(one, gs, k, total, deg, nullptr, dag_ptr, dag_col,
-                                                               dag_cap, kbits, nullptr, ctr);
+                                                               dag_cap, kbits, nullptr, nullptr, ctr);
     k_orient_hub<Off, true, BATCH><<<hg, HUB_THREADS, 0, st>>>(one, gs, k, total, hubs, deg, nullptr, dag_ptr, dag_col,
-                                                                dag_cap, kbits, nullptr, ctr);
+                                                                dag_cap, kbits, nullptr, nullptr, ctr);
     return cudaGetLastError();
 }
 
@@ -646,14 +658,14 @@ int scan_blocks(int64_t n) { return (int)((n + SCAN_TILE - 1) / SCAN_TILE); }
 cudaError_t launch_orient(const void* row_ptr, int offset_bits, const int32_t* col, int64_t n, int64_t nnz,
                           int32_t* deg, int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
                           int64_t dag_cap, int32_t* hubs, unsigned* kbits, DevCounters* ctr, int num_sms,
-                          cudaStream_t st, long long* launches, int32_t* start32, int32_t* rdag) {
+                          cudaStream_t st, long long* launches, int2* bnd, int32_t* rdag) {
     const GraphRef one{row_ptr, col, n, nnz, 0};
     const int64_t words = keep_bits_words(nnz);
     if (offset_bits == 64)
         return orient_t<long long, false>(one, nullptr, 1, n, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs,
-                                          kbits, words, start32, rdag, ctr, num_sms, st, launches);
+                                          kbits, words, bnd, rdag, ctr, num_sms, st, launches);
     return orient_t<int32_t, false>(one, nullptr, 1, n, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs, kbits,
-                                    words, start32, rdag, ctr, num_sms, st, launches);
+                                    words, bnd, rdag, ctr, num_sms, st, launches);
 }
 
 cudaError_t launch_orient_batch(const GraphRef* graphs, int k, int offset_bits, int64_t total, int32_t* deg,
@@ -670,12 +682,12 @@ cudaError_t launch_orient_batch(const GraphRef* graphs, int k, int offset_bits, 
 
 cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* warp_desc,
                        int2* items, int64_t item_cap, DevCounters* ctr, int num_sms, cudaStream_t st,
-                       long long* launches, const int32_t* dag_len, long long max_m) {
+                       long long* launches, const int2* dag_bnd, long long max_m) {
     if (n <= 0) return cudaSuccess;
     *launches += 1;
     int g = (int)((n + 255) / 256);
     if (g > num_sms * 16) g = num_sms * 16;
-    k_bin<<<g, 256, 0, st>>>(dag_ptr, dag_len, n, cfg.warp_max_out_degree, cfg.item_neighbors, cfg.shard_count,
+    k_bin<<<g, 256, 0, st>>>(dag_ptr, dag_bnd, n, cfg.warp_max_out_degree, cfg.item_neighbors, cfg.shard_count,
                              cfg.shard_index, warp_list, warp_desc, items, item_cap, max_m, ctr);
     return cudaGetLastError();
 }

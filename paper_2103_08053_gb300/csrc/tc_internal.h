@@ -86,15 +86,15 @@ int scan_blocks(int64_t n);
 // records each entry's keep decision there and the compaction pass reads it
 // instead of gathering the neighbours' degrees a second time.
 inline int64_t keep_bits_words(int64_t nnz) { return (nnz >> 5) + 2; }
-// Row-local mode (start32 and rdag given, nnz < 2^31): the DAG is left where
-// the CSR has it -- N+(u) = rdag[start32[u], start32[u] + kept[u]), start32 =
-// row_ptr as int32 (n+1 entries), rdag of nnz entries -- by the count pass
-// alone (no scan, no compaction), and ctr->m receives the number of kept
-// entries; dag_ptr, dag_col and kbits are then unused.
+// Row-local mode (bnd and rdag given, nnz < 2^31): the DAG is left where the
+// CSR has it -- N+(u) = rdag[bnd[u].x, bnd[u].x + bnd[u].y), bnd[u] = (row_ptr[u],
+// d+(u)), bnd[n].x = nnz, rdag of nnz entries -- by the count pass alone (no
+// scan, no compaction), and ctr->m receives the number of kept entries;
+// kept, dag_ptr, dag_col and kbits are then unused.
 cudaError_t launch_orient(const void* row_ptr, int offset_bits, const int32_t* col, int64_t n, int64_t nnz,
                           int32_t* deg, int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
                           int64_t dag_cap, int32_t* hubs, unsigned* kbits, DevCounters* ctr, int num_sms,
-                          cudaStream_t st, long long* launches, int32_t* start32 = nullptr, int32_t* rdag = nullptr);
+                          cudaStream_t st, long long* launches, int2* bnd = nullptr, int32_t* rdag = nullptr);
 
 // Orientation of k graphs at once (device array of GraphRef, bases ascending)
 // into one DAG over the padded global vertex space [0, total).
@@ -107,13 +107,13 @@ cudaError_t launch_orient_batch(const GraphRef* graphs, int k, int offset_bits, 
 cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* warp_desc,
                        int2* items, int64_t item_cap, DevCounters* ctr, int num_sms, cudaStream_t st,
                        long long* launches,
-                       const int32_t* dag_len = nullptr, long long max_m = -1);
+                       const int2* dag_bnd = nullptr, long long max_m = -1);
 
 // ---- counting (count.cu) ----------------------------------------------------
 cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t n, const int32_t* warp_list,
                          const int2* warp_desc, const int2* items, unsigned long long* per_vertex,
                          const CountCfg& cfg, DevCounters* ctr, cudaStream_t st, long long* launches,
-                         const int32_t* dag_len = nullptr);
+                         const int2* dag_bnd = nullptr);
 int count_block_budget_ints(const CountCfg& cfg);
 int count_block_part_max(const CountCfg& cfg);
 // ints of one warp-worker table for out-degree d (2*nextpow2(d) buckets of 4 slots + byte lengths)
