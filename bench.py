@@ -430,6 +430,19 @@ def run_gb300(args):
     torch.cuda.synchronize(dev)
     e2e_ms = (time.perf_counter() - t_e) * 1e3 / e2e_steps
     _, e2e_ms = shard.combine(0, e2e_ms, device=dev)
+    # the host-to-device copy alone on this machine (context for the end-to-end number)
+    rp_d = torch.empty_like(rp_pin, device=dev)
+    col_d = torch.empty_like(col_pin, device=dev)
+    h0 = torch.cuda.Event(enable_timing=True)
+    h1 = torch.cuda.Event(enable_timing=True)
+    h0.record(stream)
+    for _ in range(3):
+        rp_d.copy_(rp_pin, non_blocking=True)
+        col_d.copy_(col_pin, non_blocking=True)
+    h1.record(stream)
+    torch.cuda.synchronize(dev)
+    h2d_ms = h0.elapsed_time(h1) / 3
+    del rp_d, col_d
     ctx.read_timing()
     ctx.close()
 
@@ -468,7 +481,7 @@ def run_gb300(args):
                      "bytes_model": "4(n+1) + 12m + 4W+"},
         "e2e": {"value": g.m / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(rp_h.nbytes + col_h.nbytes), "d2h_bytes_per_step": 16,
-                "api": "tc_count_host (pinned host CSR)"},
+                "h2d_copy_ms": h2d_ms, "api": "tc_count_host (pinned host CSR)"},
         "gpu_launches": launches,
         "clocks": clocks,
     }

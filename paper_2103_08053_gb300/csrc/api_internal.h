@@ -74,6 +74,7 @@ struct BatchRunner {
     DevCounters* h_ctr = nullptr;   // pinned
     int h_cap = 0;
     int k = 0, bits = 32;
+    bool row_local = false;         // the batch's DAG is row-local (see launch_orient)
     long long total = 0, nnz_total = 0;
     bool moved = true;              // a buffer moved since the graph was captured
     cudaGraphExec_t exec = nullptr;

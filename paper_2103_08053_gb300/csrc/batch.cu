@@ -116,18 +116,25 @@ tc_status BatchRunner::prepare(tc_ctx* ctx, const tc_csr* gs, int k) {
         if (s) return s;
         moved = true;
     }
-    long long base = 0;
+    long long base = 0, ebase = 0;
     for (int i = 0; i < k; ++i) {
-        h_graphs[i] = GraphRef{gs[i].row_ptr, gs[i].col, gs[i].n, gs[i].nnz, base};
+        h_graphs[i] = GraphRef{gs[i].row_ptr, gs[i].col, gs[i].n, gs[i].nnz, base, ebase};
         base += (gs[i].n + 31) / 32 * 32;
+        ebase += gs[i].nnz;
     }
+    // row-local DAG (lists left in the rows' slots of one array of all the
+    // batch's entries) when the entry offsets fit int32
+    row_local = nnz_total < 0x7fffffffLL && !ctx->cfg.edge_centric;
     tc_status s;
     bool mv = false;
     if ((s = ensure_tracked(ctx, graphs, sizeof(GraphRef) * (size_t)k, stream, mv))) return s;
     if ((s = ensure_tracked(ctx, counts, sizeof(uint64_t) * (size_t)k, stream, mv))) return s;
     if ((s = ensure_tracked(ctx, per_vertex, sizeof(uint64_t) * (size_t)(total + 1), stream, mv))) return s;
     if ((s = ensure_tracked(ctx, dag_ptr, sizeof(int32_t) * (size_t)(total + 1), stream, mv))) return s;
-    if ((s = ensure_tracked(ctx, dag_col, sizeof(int32_t) * (size_t)(nnz_total / 2 + 1), stream, mv))) return s;
+    if ((s = ensure_tracked(ctx, dag_col, sizeof(int32_t) * (size_t)(row_local ? nnz_total + 1 : nnz_total / 2 + 1),
+                            stream, mv)))
+        return s;
+    if (row_local && (s = ensure_tracked(ctx, ws.bnd, sizeof(int2) * (size_t)(total + 1), stream, mv))) return s;
     if ((s = ensure_tracked(ctx, ws.deg, (size_t)(total + 1) * 4, stream, mv))) return s;
     if ((s = ensure_tracked(ctx, ws.kept, (size_t)(total + 1) * 4, stream, mv))) return s;
     if ((s = ensure_tracked(ctx, ws.partial, (size_t)(scan_blocks(total) + 2) * 8, stream, mv))) return s;
@@ -150,14 +157,16 @@ tc_status BatchRunner::enqueue(tc_ctx* ctx) {
     cudaError_t e = cudaMemcpyAsync(graphs.p, h_graphs, sizeof(GraphRef) * (size_t)k, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, sizeof(DevCounters), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(per_vertex.p, 0, sizeof(uint64_t) * (size_t)total, stream);
+    int2* bnd = row_local ? (int2*)ws.bnd.p : nullptr;
     if (e == cudaSuccess)
         e = launch_orient_batch((const GraphRef*)graphs.p, k, bits, total, (int32_t*)ws.deg.p, (int32_t*)ws.kept.p,
                                 (long long*)ws.partial.p, (int32_t*)dag_ptr.p, (int32_t*)dag_col.p,
-                                nnz_total / 2 + 1, (int32_t*)ws.hubs.p, ctr, ctx->num_sms, stream, &nl);
+                                nnz_total / 2 + 1, (int32_t*)ws.hubs.p, ctr, ctx->num_sms, stream, &nl, bnd,
+                                row_local ? (int32_t*)dag_col.p : nullptr, nnz_total);
     if (e == cudaSuccess)
         e = launch_bin((const int32_t*)dag_ptr.p, total, ctx->cfg, (int32_t*)ws.warp_list.p, (int2*)ws.warp_desc.p,
                        (int2*)ws.items.p, (int64_t)(ws.items.bytes / sizeof(int2)), ctr, ctx->num_sms, stream,
-                       &nl);
+                       &nl, bnd, row_local ? nnz_total / 2 : -1);
     CountCfg cfg = ctx->cfg;
     if (grid_share < 1.0f) {  // leave SMs to runners on other streams
         cfg.warp_grid = cfg.warp_grid * grid_share < 1.0f ? 1 : (int)(cfg.warp_grid * grid_share);
@@ -166,7 +175,7 @@ tc_status BatchRunner::enqueue(tc_ctx* ctx) {
     if (e == cudaSuccess)
         e = launch_count((const int32_t*)dag_ptr.p, (const int32_t*)dag_col.p, total,
                          (const int32_t*)ws.warp_list.p, (const int2*)ws.warp_desc.p, (const int2*)ws.items.p,
-                         (unsigned long long*)per_vertex.p, cfg, ctr, stream, &nl);
+                         (unsigned long long*)per_vertex.p, cfg, ctr, stream, &nl, bnd);
     if (e == cudaSuccess) {
         k_segsum<<<k, 256, 0, stream>>>((const unsigned long long*)per_vertex.p, (const GraphRef*)graphs.p,
                                         (unsigned long long*)counts.p);

@@ -46,7 +46,7 @@ __device__ __forceinline__ GraphRef graph_of(int64_t row, const GraphRef& one, c
 template <typename Off, bool BATCH>
 __global__ void k_degree(GraphRef one, const GraphRef* __restrict__ gs, int k, int64_t total,
                          int32_t* __restrict__ deg, int32_t* __restrict__ hubs, int2* __restrict__ bnd,
-                         DevCounters* ctr) {
+                         long long entries, DevCounters* ctr) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < total; u += stride) {
         const GraphRef G = graph_of<BATCH>(u, one, gs, k);
@@ -62,8 +62,8 @@ __global__ void k_degree(GraphRef one, const GraphRef* __restrict__ gs, int k, i
             }
         }
         deg[u] = (int32_t)d;
-        if (!BATCH && bnd && u == total - 1)  // row-local DAG: entries readable past the last list
-            bnd[total] = make_int2((int32_t)static_cast<const Off*>(G.row_ptr)[ul + 1], 0);
+        if (bnd && u == total - 1)  // row-local DAG: the entries readable past the last list
+            bnd[total] = make_int2((int32_t)entries, 0);
         if (d > HUB_DEGREE) hubs[atomicAdd(&ctr->n_hub, 1)] = (int32_t)u;
         else if (d > MID_DEGREE) hubs[total - 1 - atomicAdd(&ctr->n_mid, 1)] = (int32_t)u;  // from the back
     }
@@ -119,7 +119,10 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
         const int nr = (int)(n - u0 < 32 ? (n - u0 > 0 ? n - u0 : 0) : 32);
         const int64_t row0 = BATCH ? g * 32 : u0;  // index of the group's first row in kept / dag_ptr
         if (nr == 0) {  // padding rows of a batch
-            if (!COMPACT) kept[g * 32 + lane] = 0;
+            if (!COMPACT) {
+                if (bnd) bnd[g * 32 + lane] = make_int2(0, 0);
+                else kept[g * 32 + lane] = 0;
+            }
             continue;
         }
         long long e = 0;
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
         // rows walked here: non-empty and not hubs (the hub kernel takes those)
         const bool walk = lane < nr && len > 0 && len <= MID_DEGREE;
         if (!COMPACT && (BATCH || lane < nr) && !walk) {  // mid and hub rows: rewritten later
-            if (bnd) bnd[row0 + lane] = make_int2((int)a, 0);
+            if (bnd) bnd[row0 + lane] = make_int2((int)(G.ebase + a), 0);
             else kept[row0 + lane] = 0;
         }
         const unsigned wm = __ballot_sync(FULL, walk);
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
                     if (keep) {
                         const long long pos = (long long)next + __popc(km & lt & ~((1u << first) - 1u));
                         if (!COMPACT)
-                            rdag[pos] = (int32_t)v;
+                            rdag[G.ebase + pos] = (int32_t)(vb + v);
                         else if (pos < dag_cap)
                             dag_col[pos] = (int32_t)(vb + v);
                         else
@@ -246,7 +249,7 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
             }
         }
         if (!COMPACT && lst) {
-            if (bnd) bnd[row0 + rid] = make_int2((int)ca, cnt);  // row-local DAG: (start, d+)
+            if (bnd) bnd[row0 + rid] = make_int2((int)(G.ebase + ca), cnt);  // row-local DAG: (start, d+)
             else kept[row0 + rid] = cnt;
         }
         if (!COMPACT && rdag) {  // kept entries of the walk, for the symmetry check
@@ -293,9 +296,9 @@ __global__ void __launch_bounds__(HUB_THREADS)
         __syncthreads();
         // output: the compacted DAG, or (row-local count pass) the row itself
         const bool write = COMPACT || rdag;
-        int32_t* out = COMPACT ? dag_col : rdag;
+        int32_t* out = COMPACT ? dag_col : rdag + G.ebase;
         const long long ocap = COMPACT ? dag_cap : 0x7fffffffffffffffLL;
-        const int64_t obase = COMPACT ? G.vbase : 0;
+        const int64_t obase = G.vbase;
         long long pos0 = COMPACT ? (long long)dag_ptr[ug] : a;
         int total = 0;
         for (long long t0 = a; t0 < b; t0 += 4LL * HUB_THREADS) {
@@ -381,7 +384,7 @@ __global__ void __launch_bounds__(HUB_THREADS)
             if (threadIdx.x == 0) {
                 int t = 0;
                 for (int i = 0; i < nw; ++i) t += s_w[i];
-                if (bnd) bnd[ug] = make_int2((int)a, t);
+                if (bnd) bnd[ug] = make_int2((int)(G.ebase + a), t);
                 else kept[ug] = t;
                 if (rdag && t) atomicAdd(reinterpret_cast<unsigned long long*>(&ctr->m), (unsigned long long)t);
             }
@@ -440,8 +443,8 @@ __global__ void __launch_bounds__(HUB_THREADS)
                 const long long p0 = rb + __popc(km0 & lt);
                 const long long p1 = rb + __popc(km0) + __popc(km1 & lt);
                 if (!COMPACT) {
-                    if (k0) rdag[p0] = v0;
-                    if (k1) rdag[p1] = v1;
+                    if (k0) rdag[G.ebase + p0] = (int32_t)(G.vbase + v0);
+                    if (k1) rdag[G.ebase + p1] = (int32_t)(G.vbase + v1);
                 } else {
                     if (k0) {
                         if (p0 < dag_cap) dag_col[p0] = (int32_t)(G.vbase + v0);
@@ -456,7 +459,7 @@ __global__ void __launch_bounds__(HUB_THREADS)
             rc += __popc(km0) + __popc(km1);
         }
         if (!COMPACT && lane == 0) {
-            if (bnd) bnd[ug] = make_int2((int)ra, rc);
+            if (bnd) bnd[ug] = make_int2((int)(G.ebase + ra), rc);
             else kept[ug] = rc;
             if (rdag && rc) atomicAdd(reinterpret_cast<unsigned long long*>(&ctr->m), (unsigned long long)rc);
         }
@@ -618,8 +621,8 @@ __global__ void k_bin(const int32_t* __restrict__ dag_ptr, const int2* __restric
 template <typename Off, bool BATCH>
 cudaError_t orient_t(const GraphRef& one, const GraphRef* gs, int k, int64_t total, int32_t* deg, int32_t* kept,
                      long long* partial, int32_t* dag_ptr, int32_t* dag_col, int64_t dag_cap, int32_t* hubs,
-                     unsigned* kbits, int64_t kbits_words, int2* bnd, int32_t* rdag, DevCounters* ctr,
-                     int num_sms, cudaStream_t st, long long* launches) {
+                     unsigned* kbits, int64_t kbits_words, int2* bnd, int32_t* rdag, long long entries,
+                     DevCounters* ctr, int num_sms, cudaStream_t st, long long* launches) {
     if (total <= 0) return cudaSuccess;
     if (rdag) kbits = nullptr;  // the row-local DAG needs no compaction pass
     if (kbits) {
@@ -634,7 +637,7 @@ cudaError_t orient_t(const GraphRef& one, const GraphRef* gs, int k, int64_t tot
     if (og > og_cap) og = og_cap;
     int dg = (int)((total + 255) / 256);
     if (dg > num_sms * 16) dg = num_sms * 16;
-    k_degree<Off, BATCH><<<dg, 256, 0, st>>>(one, gs, k, total, deg, hubs, bnd, ctr);
+    k_degree<Off, BATCH><<<dg, 256, 0, st>>>(one, gs, k, total, deg, hubs, bnd, entries, ctr);
     k_orient<Off, false, BATCH><<<og, ORIENT_THREADS, 0, st>>>(one, gs, k, total, deg, kept, nullptr, nullptr, 0,
                                                                 kbits, rdag, bnd, ctr);
     k_orient_hub<Off, false, BATCH><<<hg, HUB_THREADS, 0, st>>>(one, gs, k, total, hubs, deg, kept, nullptr, nullptr, 0,
@@ -659,25 +662,25 @@ cudaError_t launch_orient(const void* row_ptr, int offset_bits, const int32_t* c
                           int32_t* deg, int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
                           int64_t dag_cap, int32_t* hubs, unsigned* kbits, DevCounters* ctr, int num_sms,
                           cudaStream_t st, long long* launches, int2* bnd, int32_t* rdag) {
-    const GraphRef one{row_ptr, col, n, nnz, 0};
+    const GraphRef one{row_ptr, col, n, nnz, 0, 0};
     const int64_t words = keep_bits_words(nnz);
     if (offset_bits == 64)
         return orient_t<long long, false>(one, nullptr, 1, n, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs,
-                                          kbits, words, bnd, rdag, ctr, num_sms, st, launches);
+                                          kbits, words, bnd, rdag, nnz, ctr, num_sms, st, launches);
     return orient_t<int32_t, false>(one, nullptr, 1, n, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs, kbits,
-                                    words, bnd, rdag, ctr, num_sms, st, launches);
+                                    words, bnd, rdag, nnz, ctr, num_sms, st, launches);
 }
 
 cudaError_t launch_orient_batch(const GraphRef* graphs, int k, int offset_bits, int64_t total, int32_t* deg,
                                 int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
                                 int64_t dag_cap, int32_t* hubs, DevCounters* ctr, int num_sms, cudaStream_t st,
-                                long long* launches) {
-    const GraphRef none{nullptr, nullptr, 0, 0, 0};
+                                long long* launches, int2* bnd, int32_t* rdag, long long entries) {
+    const GraphRef none{nullptr, nullptr, 0, 0, 0, 0};
     if (offset_bits == 64)
         return orient_t<long long, true>(none, graphs, k, total, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs,
-                                         nullptr, 0, nullptr, nullptr, ctr, num_sms, st, launches);
+                                         nullptr, 0, bnd, rdag, entries, ctr, num_sms, st, launches);
     return orient_t<int32_t, true>(none, graphs, k, total, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs,
-                                   nullptr, 0, nullptr, nullptr, ctr, num_sms, st, launches);
+                                   nullptr, 0, bnd, rdag, entries, ctr, num_sms, st, launches);
 }
 
 cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* warp_desc,

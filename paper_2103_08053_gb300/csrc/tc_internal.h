@@ -69,6 +69,7 @@ struct GraphRef {
     const void* row_ptr;  // int32 or int64 offsets (one width per pass)
     const int32_t* col;
     long long n, nnz, vbase;
+    long long ebase;      // row-local DAG: offset of this graph's entries in the shared array
 };
 
 // ---- orientation (orient.cu) ----------------------------------------------
@@ -101,7 +102,8 @@ cudaError_t launch_orient(const void* row_ptr, int offset_bits, const int32_t* c
 cudaError_t launch_orient_batch(const GraphRef* graphs, int k, int offset_bits, int64_t total, int32_t* deg,
                                 int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
                                 int64_t dag_cap, int32_t* hubs, DevCounters* ctr, int num_sms, cudaStream_t st,
-                                long long* launches);
+                                long long* launches,
+                                int2* bnd = nullptr, int32_t* rdag = nullptr, long long entries = 0);
 
 // Binning (Sec. 4.3) from an existing DAG: fills warp_list / items / counters.
 cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* warp_desc,

@@ -55,7 +55,7 @@ def test_batch_replay_with_new_graphs_of_the_same_shape(T):
             assert c.count_batch([dev(g) for g in batch]) == want
         l0 = c.kernel_launches()
         c.count_batch([dev(g) for g in a])
-        assert c.kernel_launches() - l0 == 12  # 8 orientation + bin + 2 counting + segsum, replayed
+        assert c.kernel_launches() - l0 == 7  # 3 orientation + bin + 2 counting + segsum, replayed
 
 
 def test_batch_int64_offsets_and_block_vertices(T):
