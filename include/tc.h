@@ -193,7 +193,10 @@ tc_status tc_count_async(tc_ctx* ctx, const tc_csr* g, uint64_t* count_device, i
 tc_status tc_reserve(tc_ctx* ctx, int64_t n, int64_t nnz);
 
 /* The whole path from host memory: copies the host CSR g to the device,
- * orients, counts, and copies the count back. Blocks. */
+ * orients, counts, and copies the count back. Blocks. A graph of at least
+ * 2^20 entries (and fewer than 2^31) has its neighbour lists copied in row
+ * pieces on a second stream, each piece oriented as soon as it has landed;
+ * with page-locked host arrays the copy and the orientation overlap. */
 tc_status tc_count_host(tc_ctx* ctx, const tc_csr* g, uint64_t* count_host, void* stream);
 
 /* Exact statistics of an oriented graph (out-degree bins, W+). Blocks. */

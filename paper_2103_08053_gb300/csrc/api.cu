@@ -380,6 +380,9 @@ tc_status tc_destroy(tc_ctx* ctx) {
             cudaFree(kv.second);
         }
         ctx->dags.clear();
+        for (cudaEvent_t& e : ctx->aux_ev)
+            if (e) cudaEventDestroy(e);
+        if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
         if (ctx->host_ctr) cudaFreeHost(ctx->host_ctr);
         ctx->host_ctr = nullptr;
     }
@@ -563,12 +566,106 @@ tc_status tc_count(tc_ctx* ctx, const tc_csr* g, uint64_t* count_host, void* str
     return TC_OK;
 }
 
+// tc_count_host for a graph that takes the row-local path: the neighbour
+// lists are copied in kHostPieces pieces (row ranges of about equal entries,
+// cut at 32-row groups) on a second stream, and the orientation's count pass
+// runs on each piece as soon as it has landed, so orientation overlaps the
+// transfer instead of following it.
+constexpr int kHostPieces = 8;
+static tc_status count_host_pieces(tc_ctx* ctx, const tc_csr* g, uint64_t* count_host, cudaStream_t st) {
+    Workspace& ws = ctx->ws;
+    const int64_t n = g->n, nnz = g->nnz;
+    const size_t rp_bytes = (size_t)(n + 1) * (g->offset_bits / 8);
+    tc_status s;
+    if ((s = ctx->csr_copy.a.ensure(ctx, rp_bytes, st))) return s;
+    if ((s = ctx->csr_copy.b.ensure(ctx, (size_t)nnz * 4 + 4, st))) return s;
+    if ((s = ensure_orient_ws(ctx, ws, n, nnz, st))) return s;
+    if ((s = ws.bnd.ensure(ctx, (size_t)(n + 1) * 8, st))) return s;
+    if ((s = ws.dag_col.ensure(ctx, (size_t)(nnz + 1) * 4, st))) return s;
+    if (!ctx->aux_stream) {
+        s = cuda_status(ctx, cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        for (cudaEvent_t& e : ctx->aux_ev)
+            if (!s) s = cuda_status(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "cudaEventCreate");
+        if (s) return s;
+    }
+    // piece boundaries in 32-row groups, from the host row offsets
+    auto rp_at = [&](int64_t r) -> int64_t {
+        return g->offset_bits == 64 ? static_cast<const int64_t*>(g->row_ptr)[r]
+                                    : (int64_t) static_cast<const int32_t*>(g->row_ptr)[r];
+    };
+    const int64_t groups = (n + 31) / 32;
+    int64_t cuts[kHostPieces + 1];
+    cuts[0] = 0;
+    cuts[kHostPieces] = groups;
+    for (int i = 1; i < kHostPieces; ++i) {
+        const int64_t target = nnz * i / kHostPieces;
+        int64_t lo = 0, hi = n;  // first row r with rp_at(r) >= target
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) / 2;
+            if (rp_at(mid) < target) lo = mid + 1;
+            else hi = mid;
+        }
+        const int64_t gcut = lo / 32;
+        cuts[i] = gcut < cuts[i - 1] ? cuts[i - 1] : (gcut > groups ? groups : gcut);
+    }
+    cudaEvent_t* ev = ctx->aux_ev;
+    cudaError_t e = cudaEventRecord(ev[kHostPieces], st);  // earlier work on st is done with the buffers
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->aux_stream, ev[kHostPieces], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->csr_copy.a.p, g->row_ptr, rp_bytes, cudaMemcpyHostToDevice, st);
+    for (int i = 0; i < kHostPieces && e == cudaSuccess; ++i) {
+        const int64_t lo = rp_at(cuts[i] * 32 < n ? cuts[i] * 32 : n);
+        const int64_t hi = rp_at(cuts[i + 1] * 32 < n ? cuts[i + 1] * 32 : n);
+        if (hi > lo)
+            e = cudaMemcpyAsync(static_cast<int32_t*>(ctx->csr_copy.b.p) + lo, g->col + lo, (size_t)(hi - lo) * 4,
+                                cudaMemcpyHostToDevice, ctx->aux_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[i], ctx->aux_stream);
+    }
+    if ((s = cuda_status(ctx, e, "copying the CSR to the device"))) return s;
+    s = cuda_status(ctx, cudaMemsetAsync(ws.ctr.p, 0, sizeof(DevCounters), st), "memset counters");
+    TimedCall* tm = s ? nullptr : timing_begin(ctx, true);
+    timing_mark(tm, 0, st);
+    if (!s) {
+        long long nl = 0;
+        e = launch_orient_row_local_pieces(ctx->csr_copy.a.p, g->offset_bits, (const int32_t*)ctx->csr_copy.b.p, n,
+                                           nnz, (int32_t*)ws.deg.p, (int32_t*)ws.kept.p, (int32_t*)ws.hubs.p,
+                                           (int2*)ws.bnd.p, (int32_t*)ws.dag_col.p, (DevCounters*)ws.ctr.p,
+                                           ctx->num_sms, st, &nl, cuts, kHostPieces, ev);
+        ctx->launches += nl;
+        s = cuda_status(ctx, e, "orientation kernels");
+    }
+    timing_mark(tm, 1, st);
+    if (!s)
+        s = enqueue_count(ctx, ws, nullptr, (int32_t*)ws.dag_col.p, n, nullptr, st, tm, (int2*)ws.bnd.p, nnz / 2);
+    uint64_t* d_count = (uint64_t*)ctx->out_scalars.p;
+    int32_t* d_err = (int32_t*)((char*)ctx->out_scalars.p + 8);
+    if (!s) {
+        long long nl = 0;
+        s = cuda_status(ctx, launch_finish((DevCounters*)ws.ctr.p, (unsigned long long*)d_count, d_err, st, &nl),
+                        "finish kernel");
+        ctx->launches += nl;
+    }
+    if (s) return s;
+    e = cudaMemcpyAsync(ctx->host_ctr, ctx->out_scalars.p, 16, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if ((s = cuda_status(ctx, e, "reading the count"))) return s;
+    uint64_t cnt;
+    int32_t err;
+    memcpy(&cnt, ctx->host_ctr, 8);
+    memcpy(&err, (char*)ctx->host_ctr + 8, 4);
+    if (err) return ctx_fail(ctx, (tc_status)err, "%s", tc_status_string((tc_status)err));
+    *count_host = cnt;
+    return TC_OK;
+}
+
 tc_status tc_count_host(tc_ctx* ctx, const tc_csr* g, uint64_t* count_host, void* stream) {
     if (!ctx || !count_host) return TC_ERR_INVALID_ARG;
     tc_status s = check_csr(ctx, g);
     if (s) return s;
     DeviceGuard dg(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
+    if (g->n > 0 && g->nnz >= (1 << 20) && g->nnz < 0x7fffffffLL && !ctx->cfg.edge_centric &&
+        !ctx->cfg.cycle_timing)
+        return count_host_pieces(ctx, g, count_host, st);
     const size_t rp_bytes = (size_t)(g->n + 1) * (g->offset_bits / 8);
     const size_t col_bytes = (size_t)g->nnz * 4;
     if ((s = ctx->csr_copy.a.ensure(ctx, rp_bytes, st))) return s;

@@ -113,6 +113,8 @@ struct tc_ctx {
     std::vector<tcg::TimedCall> timed_free; // event sets to reuse
     long long cfg_version = 0;              // bumped by tc_set_params
     long long cyc_build = 0, cyc_probe = 0; // worker cycles read back by blocking calls (record_timing 2)
+    cudaStream_t aux_stream = nullptr;      // tc_count_host: host-to-device copies in pieces
+    cudaEvent_t aux_ev[9] = {};             // one per piece, plus the start
     tcg::BatchRunner* batch = nullptr;
     tcg::ServeState* serve = nullptr;
 };

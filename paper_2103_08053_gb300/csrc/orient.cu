@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
     k_orient(GraphRef one, const GraphRef* __restrict__ gs, int k, int64_t total, const int32_t* __restrict__ deg,
              int32_t* __restrict__ kept, const int32_t* __restrict__ dag_ptr, int32_t* __restrict__ dag_col,
              int64_t dag_cap, unsigned* __restrict__ kbits, int32_t* __restrict__ rdag, int2* __restrict__ bnd,
-             DevCounters* ctr) {
+             int64_t g_lo, int64_t g_hi, DevCounters* ctr) {
     __shared__ long long s_a[ORIENT_WARPS][32];
     __shared__ int s_len[ORIENT_WARPS][32];
     __shared__ int s_rid[ORIENT_WARPS][32];
@@ -110,7 +110,10 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned le = lanemask_le(lane), lt = lanemask_lt(lane);
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g * 32 < total; g += nw) {
+    // groups [g_lo, g_hi) of 32 rows (all of them, or one piece of a graph whose
+    // neighbour lists arrive in pieces)
+    for (int64_t g = g_lo + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); g < g_hi && g * 32 < total;
+         g += nw) {
         const GraphRef G = graph_of<BATCH>(g * 32, one, gs, k);
         const Off* row_ptr = static_cast<const Off*>(G.row_ptr);
         const int32_t* col = G.col;
@@ -639,7 +642,7 @@ cudaError_t orient_t(const GraphRef& one, const GraphRef* gs, int k, int64_t tot
     if (dg > num_sms * 16) dg = num_sms * 16;
     k_degree<Off, BATCH><<<dg, 256, 0, st>>>(one, gs, k, total, deg, hubs, bnd, entries, ctr);
     k_orient<Off, false, BATCH><<<og, ORIENT_THREADS, 0, st>>>(one, gs, k, total, deg, kept, nullptr, nullptr, 0,
-                                                                kbits, rdag, bnd, ctr);
+                                                                kbits, rdag, bnd, 0, groups, ctr);
     k_orient_hub<Off, false, BATCH><<<hg, HUB_THREADS, 0, st>>>(one, gs, k, total, hubs, deg, kept, nullptr, nullptr, 0,
                                                                  kbits, rdag, bnd, ctr);
     if (rdag) return cudaGetLastError();  // row-local DAG: bnd and rdag are the DAG
@@ -648,7 +651,7 @@ cudaError_t orient_t(const GraphRef& one, const GraphRef* gs, int k, int64_t tot
     k_scan_top<<<1, SCAN_TOP_THREADS, 0, st>>>(partial, nb, dag_ptr, total, ctr);
     k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(kept, total, partial, dag_ptr);
     k_orient<Off, true, BATCH><<<og, ORIENT_THREADS, 0, st>>>(one, gs, k, total, deg, nullptr, dag_ptr, dag_col,
-                                                               dag_cap, kbits, nullptr, nullptr, ctr);
+                                                               dag_cap, kbits, nullptr, nullptr, 0, groups, ctr);
     k_orient_hub<Off, true, BATCH><<<hg, HUB_THREADS, 0, st>>>(one, gs, k, total, hubs, deg, nullptr, dag_ptr, dag_col,
                                                                 dag_cap, kbits, nullptr, nullptr, ctr);
     return cudaGetLastError();
@@ -671,6 +674,32 @@ cudaError_t launch_orient(const void* row_ptr, int offset_bits, const int32_t* c
                                     words, bnd, rdag, nnz, ctr, num_sms, st, launches);
 }
 
+template <typename Off>
+cudaError_t orient_pieces_t(const GraphRef& one, int32_t* deg, int32_t* kept, int32_t* hubs, int2* bnd, int32_t* rdag,
+                            DevCounters* ctr, int num_sms, cudaStream_t st, long long* launches,
+                            const int64_t* group_cuts, int pieces, const cudaEvent_t* ready) {
+    const int64_t total = one.n;
+    if (total <= 0) return cudaSuccess;
+    int dg = (int)((total + 255) / 256);
+    if (dg > num_sms * 16) dg = num_sms * 16;
+    k_degree<Off, false><<<dg, 256, 0, st>>>(one, nullptr, 1, total, deg, hubs, bnd, one.nnz, ctr);
+    *launches += 2 + pieces;
+    for (int i = 0; i < pieces; ++i) {
+        cudaError_t e = cudaStreamWaitEvent(st, ready[i], 0);
+        if (e != cudaSuccess) return e;
+        const int64_t glo = group_cuts[i], ghi = group_cuts[i + 1];
+        if (ghi <= glo) continue;
+        int og = (int)((ghi - glo + ORIENT_WARPS - 1) / ORIENT_WARPS);
+        const int og_cap = num_sms * 8 * 4;
+        if (og > og_cap) og = og_cap;
+        k_orient<Off, false, false><<<og, ORIENT_THREADS, 0, st>>>(one, nullptr, 1, total, deg, kept, nullptr, nullptr,
+                                                                   0, nullptr, rdag, bnd, glo, ghi, ctr);
+    }
+    k_orient_hub<Off, false, false><<<num_sms * 2, HUB_THREADS, 0, st>>>(one, nullptr, 1, total, hubs, deg, kept,
+                                                                       nullptr, nullptr, 0, nullptr, rdag, bnd, ctr);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_orient_batch(const GraphRef* graphs, int k, int offset_bits, int64_t total, int32_t* deg,
                                 int32_t* kept, long long* partial, int32_t* dag_ptr, int32_t* dag_col,
                                 int64_t dag_cap, int32_t* hubs, DevCounters* ctr, int num_sms, cudaStream_t st,
@@ -681,6 +710,19 @@ cudaError_t launch_orient_batch(const GraphRef* graphs, int k, int offset_bits, 
                                          nullptr, 0, bnd, rdag, entries, ctr, num_sms, st, launches);
     return orient_t<int32_t, true>(none, graphs, k, total, deg, kept, partial, dag_ptr, dag_col, dag_cap, hubs,
                                    nullptr, 0, bnd, rdag, entries, ctr, num_sms, st, launches);
+}
+
+cudaError_t launch_orient_row_local_pieces(const void* row_ptr, int offset_bits, const int32_t* col, int64_t n,
+                                           int64_t nnz, int32_t* deg, int32_t* kept, int32_t* hubs, int2* bnd,
+                                           int32_t* rdag, DevCounters* ctr, int num_sms, cudaStream_t st,
+                                           long long* launches, const int64_t* group_cuts, int pieces,
+                                           const cudaEvent_t* ready) {
+    const GraphRef one{row_ptr, col, n, nnz, 0, 0};
+    if (offset_bits == 64)
+        return orient_pieces_t<long long>(one, deg, kept, hubs, bnd, rdag, ctr, num_sms, st, launches, group_cuts,
+                                          pieces, ready);
+    return orient_pieces_t<int32_t>(one, deg, kept, hubs, bnd, rdag, ctr, num_sms, st, launches, group_cuts, pieces,
+                                    ready);
 }
 
 cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* warp_desc,

@@ -97,6 +97,16 @@ cudaError_t launch_orient(const void* row_ptr, int offset_bits, const int32_t* c
                           int64_t dag_cap, int32_t* hubs, unsigned* kbits, DevCounters* ctr, int num_sms,
                           cudaStream_t st, long long* launches, int2* bnd = nullptr, int32_t* rdag = nullptr);
 
+// Row-local orientation of one graph whose col arrives on the device in
+// pieces: the degree kernel, then the count pass over the 32-row groups
+// [group_cuts[i], group_cuts[i+1]) once event ready[i] has completed (the
+// copy of those rows' lists), then the hub / mid rows (after every piece).
+cudaError_t launch_orient_row_local_pieces(const void* row_ptr, int offset_bits, const int32_t* col, int64_t n,
+                                           int64_t nnz, int32_t* deg, int32_t* kept, int32_t* hubs, int2* bnd,
+                                           int32_t* rdag, DevCounters* ctr, int num_sms, cudaStream_t st,
+                                           long long* launches, const int64_t* group_cuts, int pieces,
+                                           const cudaEvent_t* ready);
+
 // Orientation of k graphs at once (device array of GraphRef, bases ascending)
 // into one DAG over the padded global vertex space [0, total).
 cudaError_t launch_orient_batch(const GraphRef* graphs, int k, int offset_bits, int64_t total, int32_t* deg,

@@ -377,10 +377,13 @@ def test_build_probe_cycle_split(T):
 
 
 def test_host_csr_pinned_and_pageable(ctx):
-    # tc_count_host: pageable arrays are copied first; pinned ones are read by
-    # the orientation's count pass directly, which writes the device copy
+    # tc_count_host from pageable and pinned host arrays; graphs of 2^20 or more
+    # entries are copied in row pieces that are oriented as they land (the last
+    # graph, with hub, mid and ragged rows), smaller ones in one copy
     gs = [G.disjoint_union([G.star(3000), G.complete(300), G.rmat(12, 16, seed=33)]),
-          G.rgg(20_000, 30.0, seed=34), G.empty(9), G.complete(3)]
+          G.rgg(20_000, 30.0, seed=34), G.empty(9), G.complete(3),
+          G.disjoint_union([G.rgg(30_001, 40.0, seed=35), G.star(5000), G.wheel(700),
+                            G.rmat(14, 16, seed=36), G.complete(45)])]
     for g in gs:
         want = oracle.count(g)
         for bits in (32, 64):
