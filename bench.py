@@ -282,7 +282,7 @@ def time_count(ctx, torch, dev, n, rp, col, reps=10):
         e1.synchronize()
         ts.append(e0.elapsed_time(e1))
     if int(err.item()) != 0:
-        raise SystemExit("counting failed during the reordering study")
+        raise SystemExit("counting failed during a study")
     return statistics.median(ts), int(out.item())
 
 
@@ -322,11 +322,20 @@ def measure_reorder(T, torch, dev, graphs):
 
 
 def measure_ablation(T, torch, dev, graphs):
-    """Sec. 3.3 and Sec. 4.2 ablations on the given graphs: the worker cycles
-    spent building tables vs probing them (vertex-centric Algorithm 1 vs the
-    edge-centric Algorithm 2, which rebuilds N+(u)'s table for every
-    out-edge), and quad vs scalar 2-hop loads. Same counts in every mode."""
-    modes = [("vertex-centric, quad loads", {}), ("vertex-centric, scalar loads", dict(scalar_loads=1)),
+    """Sec. 3.3 and Sec. 4.2 ablations on the given graphs. Sec. 3.3: the
+    worker cycles spent building tables vs probing them, vertex-centric
+    Algorithm 1 vs the edge-centric Algorithm 2 (N+(u)'s table rebuilt for
+    every out-edge). Sec. 4.2: how the warp workers spread the 2-hop lists
+    over their lanes -- virtual combination (the design, with 16-byte or
+    one-key loads) vs warp-centric, subwarps of 8 and 16 lanes and physical
+    combination. count_ms is timed without the cycle counters; the count must
+    be the same in every mode."""
+    modes = [("vertex-centric, VC, quad loads (default)", {}),
+             ("vertex-centric, VC, scalar loads", dict(scalar_loads=1)),
+             ("vertex-centric, warp-centric (WC)", dict(balance=T.TC_BALANCE_WC)),
+             ("vertex-centric, subwarp 8 (SW8)", dict(balance=T.TC_BALANCE_SW8)),
+             ("vertex-centric, subwarp 16 (SW16)", dict(balance=T.TC_BALANCE_SW16)),
+             ("vertex-centric, physical combination (PC)", dict(balance=T.TC_BALANCE_PC)),
              ("edge-centric (Algorithm 2)", dict(edge_centric=1))]
     rows = []
     for name, (n, rp, col) in graphs.items():
@@ -335,6 +344,7 @@ def measure_ablation(T, torch, dev, graphs):
             with T.Context(dev.index, params=dict(prm, record_timing=2)) as c:
                 tri = c.count(n, rp, col)          # blocking: reads the cycle counters back
                 t = c.read_timing()
+            with T.Context(dev.index, params=prm) as c:
                 ms, tri2 = time_count(c, torch, dev, n, rp, col, reps=5)
             base = tri if base is None else base
             cyc = t["build_cycles"] + t["probe_cycles"]
@@ -563,7 +573,7 @@ def main():
                     help="graph of the timed steps (default: the RGG 2^22 benchmark graph); the batched, serving "
                          "and study sections always use their own workloads")
     ap.add_argument("--ablation", type=int, default=1,
-                    help="1: also run the build/probe split and edge-centric / load-width ablation (rank 0)")
+                    help="1: also run the Sec. 3.3 (build/probe, edge-centric) and Sec. 4.2 (WC/SW/PC/VC) ablations (rank 0)")
     ap.add_argument("--reorder", type=int, default=1,
                     help="1: also run the Sec. 4.1 reordering study (rank 0)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,

@@ -119,8 +119,21 @@ typedef struct {
     int32_t edge_centric;        /* 1: ablation of Sec. 3.3's edge-centric design (Algorithm 2): the table
                                     of N+(u) is rebuilt for every out-edge (u, v) and probed with N+(v);
                                     slow by design, same counts (default 0) */
-    int32_t reserved[1];
+    int32_t balance;             /* how a warp worker spreads the 2-hop lists of its out-edges over its
+                                    lanes (Sec. 4.2; TC_BALANCE_*): virtual combination (default) or one
+                                    of the alternatives the paper compares it with. Same counts in every
+                                    mode. The alternatives need hash_mode 0 and apply to the warp
+                                    workers; thread-block workers always use virtual combination. */
 } tc_params;
+
+/* tc_params.balance (Sec. 4.2's intra-vertex workload balancing methods) */
+#define TC_BALANCE_VC 0   /* virtual combination: the lists of up to 32 out-edges form one virtual
+                             array whose indices are dealt to the lanes (default) */
+#define TC_BALANCE_WC 1   /* warp-centric: the whole warp walks one list after another */
+#define TC_BALANCE_SW8 2  /* subwarps of 8 lanes, one list each */
+#define TC_BALANCE_SW16 3 /* subwarps of 16 lanes, one list each */
+#define TC_BALANCE_PC 4   /* physical combination: the lists are copied into one combined array in
+                             device memory (per warp, rounds of 1024 entries), then walked by all lanes */
 
 /* Per-DAG statistics (tc_dag_stats), all exact:
  * wedges_plus = W+ = sum_u sum_{v in N+(u)} d+(v), the number of hash probes

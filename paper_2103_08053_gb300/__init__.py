@@ -12,7 +12,8 @@ import ctypes
 import numpy as np
 
 from . import _tc
-from ._tc import (TC_REORDER_COLLECTIVE, TC_REORDER_INDEGREE, TC_ERR_BAD_GRAPH, TC_ERR_BUSY, TC_ERR_CUDA, TC_ERR_INVALID_ARG, TC_ERR_NOT_READY, TC_ERR_OOM,
+from ._tc import (TC_BALANCE_PC, TC_BALANCE_SW8, TC_BALANCE_SW16, TC_BALANCE_VC, TC_BALANCE_WC,
+                  TC_REORDER_COLLECTIVE, TC_REORDER_INDEGREE, TC_ERR_BAD_GRAPH, TC_ERR_BUSY, TC_ERR_CUDA, TC_ERR_INVALID_ARG, TC_ERR_NOT_READY, TC_ERR_OOM,
                   TC_ERR_TIMEOUT, TC_ERR_UNSUPPORTED, TC_OK, tc_csr, tc_dag, tc_params, tc_stats, tc_timing)
 
 __all__ = ["Context", "TcError", "Dag", "default_params", "tc_csr", "tc_dag", "tc_params", "tc_stats"]

@@ -40,6 +40,13 @@ TC_ERR_UNSUPPORTED = 8
 TC_REORDER_INDEGREE = 1
 TC_REORDER_COLLECTIVE = 2
 
+# tc_params.balance (Sec. 4.2)
+TC_BALANCE_VC = 0
+TC_BALANCE_WC = 1
+TC_BALANCE_SW8 = 2
+TC_BALANCE_SW16 = 3
+TC_BALANCE_PC = 4
+
 
 class tc_csr(ctypes.Structure):
     _fields_ = [("n", c_int64), ("nnz", c_int64), ("row_ptr", c_void_p), ("offset_bits", c_int32),
@@ -56,7 +63,7 @@ class tc_params(ctypes.Structure):
                 ("item_neighbors", c_int32), ("chunk", c_int32), ("warps_per_block", c_int32),
                 ("shard_count", c_int32), ("shard_index", c_int32), ("validate", c_int32),
                 ("record_timing", c_int32), ("hash_mode", c_int32), ("scalar_loads", c_int32),
-                ("edge_centric", c_int32), ("reserved", c_int32 * 1)]
+                ("edge_centric", c_int32), ("balance", c_int32)]
 
 
 class tc_timing(ctypes.Structure):

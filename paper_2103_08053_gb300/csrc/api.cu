@@ -128,6 +128,7 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         p.hash_mode = in->hash_mode;
         p.scalar_loads = in->scalar_loads;
         p.edge_centric = in->edge_centric;
+        p.balance = in->balance;
 #undef TAKE
     }
     if (p.warp_max_out_degree < 1 || p.warp_max_out_degree > 255)
@@ -154,6 +155,10 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "scalar_loads must be 0 or 1");
     if (p.edge_centric != 0 && p.edge_centric != 1)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "edge_centric must be 0 or 1");
+    if (p.balance < TC_BALANCE_VC || p.balance > TC_BALANCE_PC)
+        return ctx_fail(ctx, TC_ERR_INVALID_ARG, "balance must be one of TC_BALANCE_VC .. TC_BALANCE_PC");
+    if (p.balance != TC_BALANCE_VC && p.hash_mode != 0)
+        return ctx_fail(ctx, TC_ERR_INVALID_ARG, "the balance ablation modes use hash_mode 0");
     if (p.record_timing < 0 || p.record_timing > 2)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "record_timing must be 0, 1 or 2");
     if (p.chunk < 1 || p.chunk > 32) return ctx_fail(ctx, TC_ERR_INVALID_ARG, "chunk must be in [1, 32]");
@@ -185,6 +190,7 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         cfg->quad_loads = p.scalar_loads ? 0 : 1;
         cfg->cycle_timing = p.record_timing == 2 ? 1 : 0;
         cfg->edge_centric = p.edge_centric;
+        cfg->balance = p.balance;
         cfg->warp_grid = cfg->block_grid = 0;
     }
     return TC_OK;
@@ -212,6 +218,7 @@ tc_status tcg::ensure_count_ws(tc_ctx* ctx, Workspace& ws, int64_t n, int64_t m,
     if ((s = ws.items.ensure(ctx, (size_t)item_capacity(n, m, ctx->cfg.item_neighbors) * sizeof(int2), st)))
         return s;
     if ((s = ws.ctr.ensure(ctx, sizeof(DevCounters) + 64, st))) return s;
+    if (ctx->cfg.balance == TC_BALANCE_PC && (s = ws.pc.ensure(ctx, pc_scratch_bytes(ctx->cfg), st))) return s;
     return TC_OK;
 }
 
@@ -281,7 +288,7 @@ static tc_status enqueue_count(tc_ctx* ctx, Workspace& ws, const int32_t* dag_pt
         if (e == cudaSuccess)
             e = launch_count(dag_ptr, dag_col, n, (const int32_t*)ws.warp_list.p, (const int2*)ws.warp_desc.p,
                              (const int2*)ws.items.p, (unsigned long long*)per_vertex, ctx->cfg, ctr, st, &nl,
-                             dag_bnd);
+                             dag_bnd, (int2*)ws.pc.p);
     } else {
         timing_mark(tm, 2, st);
     }

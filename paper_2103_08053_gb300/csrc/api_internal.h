@@ -27,9 +27,10 @@ struct DevBuf {
 // Scratch of one counting pass.
 struct Workspace {
     DevBuf deg, kept, partial, dag_ptr, dag_col, warp_list, warp_desc, items, ctr, stats, hubs, kbits, bnd;
+    DevBuf pc;  // physical-combination scratch (tc_params.balance == TC_BALANCE_PC only)
     void release_all(tc_ctx* ctx) {
         for (DevBuf* b : {&deg, &kept, &partial, &dag_ptr, &dag_col, &warp_list, &warp_desc, &items, &ctr, &stats,
-                          &hubs, &kbits, &bnd})
+                          &hubs, &kbits, &bnd, &pc})
             b->release(ctx);
     }
 };

@@ -146,6 +146,8 @@ tc_status BatchRunner::prepare(tc_ctx* ctx, const tc_csr* gs, int k) {
                             mv)))
         return s;
     if ((s = ensure_tracked(ctx, ws.ctr, sizeof(DevCounters) + 64, stream, mv))) return s;
+    if (ctx->cfg.balance == TC_BALANCE_PC && (s = ensure_tracked(ctx, ws.pc, pc_scratch_bytes(ctx->cfg), stream, mv)))
+        return s;
     if (mv) moved = true;
     return TC_OK;
 }
@@ -175,7 +177,7 @@ tc_status BatchRunner::enqueue(tc_ctx* ctx) {
     if (e == cudaSuccess)
         e = launch_count((const int32_t*)dag_ptr.p, (const int32_t*)dag_col.p, total,
                          (const int32_t*)ws.warp_list.p, (const int2*)ws.warp_desc.p, (const int2*)ws.items.p,
-                         (unsigned long long*)per_vertex.p, cfg, ctr, stream, &nl, bnd);
+                         (unsigned long long*)per_vertex.p, cfg, ctr, stream, &nl, bnd, (int2*)ws.pc.p);
     if (e == cudaSuccess) {
         k_segsum<<<k, 256, 0, stream>>>((const unsigned long long*)per_vertex.p, (const GraphRef*)graphs.p,
                                         (unsigned long long*)counts.p);

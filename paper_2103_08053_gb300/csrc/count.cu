@@ -578,6 +578,105 @@ __device__ __forceinline__ uint32_t vc_range_quad(int s, int e, int nq, int tab,
     return hits;
 }
 
+// ---- intra-vertex workload balancing alternatives (Sec. 4.2) -----------------
+// The paper compares virtual combination with three other ways of spreading
+// the 2-hop lists N+(v), v in N+(u), over a warp's lanes. They are kept here
+// as ablations of the warp workers (tc_params.balance). Each takes the same
+// input as vc_pack_quad: lane i holds N+(v_i) = dag_col[s, s + l) and the
+// table descriptor td of its out-edge (slots offset | log2 B << 16 | pack
+// slot << 21). Every key is probed with probe_one, which follows the
+// overflow chain when the home bucket is full and did not match, so the
+// count is exact for packs built with or without chains.
+
+template <bool SLOT_HITS, int HM, int SL>
+__device__ __forceinline__ uint32_t probe_one(int key, int td, const int* sm, int* stage, unsigned mult) {
+    if (key < 0) return 0;
+    const int lg = (td >> 16) & 31, tab = td & 0xffff;
+    const int h = bucket_of<HM>(key, lg, mult);
+    const Bucket<SL> b = Bucket<SL>::at(sm, tab, h);
+    int hit = b.match(key);
+    if (!hit && b.full()) hit = probe_chain<SL>(sm, tab, (1 << lg) - 1, h, key);
+    if (SLOT_HITS && hit) atomicAdd(&stage[128 + ((td >> 21) & 31)], 1);
+    return (uint32_t)hit;
+}
+
+// Warp-centric: the whole warp walks one list at a time, lane j taking
+// entries j, j + 32, ...; lanes past the end of a short list idle.
+template <bool SLOT_HITS, int HM, int SL>
+__device__ __forceinline__ uint32_t balance_wc(int s, int l, int td, const int* sm,
+                                               const int32_t* __restrict__ dag_col, int lane, int* stage,
+                                               unsigned mult) {
+    uint32_t hits = 0;
+    unsigned lists = __ballot_sync(FULL, l > 0);
+    while (lists) {
+        const int j = __ffs(lists) - 1;
+        lists &= lists - 1;
+        const int sj = __shfl_sync(FULL, s, j), lj = __shfl_sync(FULL, l, j), tdj = __shfl_sync(FULL, td, j);
+        for (int off = lane; off < lj; off += 32)
+            hits += probe_one<SLOT_HITS, HM, SL>(__ldg(dag_col + sj + off), tdj, sm, stage, mult);
+    }
+    return hits;
+}
+
+// Subwarps of S lanes: subwarp g takes the lists of lanes g, g + 32/S, ...,
+// one list per round, lane t of the subwarp taking entries t, t + S, ...; a
+// round lasts as long as its longest list.
+template <int S, bool SLOT_HITS, int HM, int SL>
+__device__ __forceinline__ uint32_t balance_sw(int s, int l, int td, const int* sm,
+                                               const int32_t* __restrict__ dag_col, int lane, int* stage,
+                                               unsigned mult) {
+    constexpr int G = 32 / S;
+    const int g = lane / S, t = lane % S;
+    const unsigned ne = __ballot_sync(FULL, l > 0);
+    const int last = ne ? 32 - __clz(ne) : 0;  // lanes [0, last) hold all the lists
+    uint32_t hits = 0;
+    for (int j0 = 0; j0 < last; j0 += G) {
+        const int j = j0 + g;  // <= 31: j0 is a multiple of G below 32
+        const int sj = __shfl_sync(FULL, s, j), lj = __shfl_sync(FULL, l, j), tdj = __shfl_sync(FULL, td, j);
+        const int lmax = (int)__reduce_max_sync(FULL, (unsigned)lj);
+        for (int off = t; off < lmax; off += S) {
+            const int key = off < lj ? __ldg(dag_col + sj + off) : NOKEY;
+            hits += probe_one<SLOT_HITS, HM, SL>(key, tdj, sm, stage, mult);
+        }
+    }
+    return hits;
+}
+
+// Physical combination: the lists are copied, one after another with the
+// whole warp, into one combined array of (key, table) pairs in this warp's
+// device-memory scratch, PC_ROUND entries per round; then every lane walks
+// the combined array, entries lane, lane + 32, ... The copy is the cost the
+// paper charges to this design.
+constexpr int PC_ROUND = 1024;
+template <bool SLOT_HITS, int HM, int SL>
+__device__ __forceinline__ uint32_t balance_pc(int s, int l, int td, const int* sm,
+                                               const int32_t* __restrict__ dag_col, int lane, int* stage,
+                                               unsigned mult, int2* buf) {
+    const int P = warp_incl_scan(l, lane);
+    const int total = __shfl_sync(FULL, P, 31);
+    const int Pex = P - l;
+    uint32_t hits = 0;
+    for (int r0 = 0; r0 < total; r0 += PC_ROUND) {
+        const int r1 = total - r0 < PC_ROUND ? total : r0 + PC_ROUND;
+        unsigned lists = __ballot_sync(FULL, l > 0 && P > r0 && Pex < r1);
+        while (lists) {
+            const int j = __ffs(lists) - 1;
+            lists &= lists - 1;
+            const int sj = __shfl_sync(FULL, s, j), pj = __shfl_sync(FULL, P, j);
+            const int xj = __shfl_sync(FULL, Pex, j), tdj = __shfl_sync(FULL, td, j);
+            const int a = xj > r0 ? xj : r0, b = pj < r1 ? pj : r1;
+            for (int f = a + lane; f < b; f += 32) buf[f - r0] = make_int2(__ldg(dag_col + sj + (f - xj)), tdj);
+        }
+        __syncwarp();
+        for (int f = lane; f < r1 - r0; f += 32) {
+            const int2 e = buf[f];
+            hits += probe_one<SLOT_HITS, HM, SL>(e.x, e.y, sm, stage, mult);
+        }
+        __syncwarp();
+    }
+    return hits;
+}
+
 // ---- workers -----------------------------------------------------------------
 
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
@@ -627,12 +726,15 @@ __device__ __forceinline__ void list_bounds(int v, const int32_t* __restrict__ d
 // smem per warp: area[area_ints] | stage[STAGE_INTS]. desc[i] = (first
 // out-edge, d+) of warp_list[i]. A pack's area holds all its tables' slots
 // first, then all their length words.
-template <bool PER_VERTEX, int HM>
+// BAL: TC_BALANCE_VC (the design) or one of the Sec. 4.2 alternatives above;
+// pc_buf: the physical combination's scratch, PC_ROUND pairs per warp.
+template <bool PER_VERTEX, int HM, int BAL>
 __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
     k_count_pack(const int32_t* __restrict__ dag_ptr, const int32_t* __restrict__ dag_col,
                  const int2* __restrict__ desc, const int32_t* __restrict__ warp_list,
                  unsigned long long* __restrict__ per_vertex, DevCounters* ctr, int n, int area_ints,
-                 int lg_min_buckets, int pop, int quad, int timing, const int2* __restrict__ dag_bnd) {
+                 int lg_min_buckets, int pop, int quad, int timing, const int2* __restrict__ dag_bnd,
+                 int2* __restrict__ pc_buf) {
     extern __shared__ int smem[];
     if (ctr->err) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -751,7 +853,19 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
                     const int e = c0 + 32 + lane;
                     list_bounds(e < E ? __ldg(dag_col + bo + e) : -1, dag_ptr, dag_bnd, n, ctr, ns, nl);
                 }
-                if (!chained && quad) {
+                if (BAL != TC_BALANCE_VC) {
+                    const int td = etab | (elg << 16) | (eslot << 21);
+                    if (BAL == TC_BALANCE_WC)
+                        hits += balance_wc<PER_VERTEX, HM, PACK_SLOTS>(s, l, td, smem, dag_col, lane, stage, mult);
+                    else if (BAL == TC_BALANCE_SW8)
+                        hits += balance_sw<8, PER_VERTEX, HM, PACK_SLOTS>(s, l, td, smem, dag_col, lane, stage, mult);
+                    else if (BAL == TC_BALANCE_SW16)
+                        hits += balance_sw<16, PER_VERTEX, HM, PACK_SLOTS>(s, l, td, smem, dag_col, lane, stage, mult);
+                    else
+                        hits += balance_pc<PER_VERTEX, HM, PACK_SLOTS>(
+                            s, l, td, smem, dag_col, lane, stage, mult,
+                            pc_buf + ((size_t)blockIdx.x * (blockDim.x >> 5) + w) * PC_ROUND);
+                } else if (!chained && quad) {
                     hits += vc_pack_quad<PER_VERTEX, HM, PACK_SLOTS>(s, l, etab | (elg << 16) | (eslot << 21), smem, dag_col,
                                                          m, lane, stage, mult);
                 } else if (!chained) {
@@ -1088,11 +1202,24 @@ __global__ void __launch_bounds__(256) k_collision(const int32_t* __restrict__ d
 int pack_smem_bytes(const CountCfg& cfg) { return cfg.warps_per_block * (cfg.warp_area_ints + STAGE_INTS) * 4; }
 
 using PackKernel = void (*)(const int32_t*, const int32_t*, const int2*, const int32_t*, unsigned long long*,
-                            DevCounters*, int, int, int, int, int, int, const int2*);
+                            DevCounters*, int, int, int, int, int, int, const int2*, int2*);
 
-PackKernel pack_kernel(bool per_vertex, int hm) {
-    if (hm == 1) return per_vertex ? k_count_pack<true, 1> : k_count_pack<false, 1>;
-    return per_vertex ? k_count_pack<true, 0> : k_count_pack<false, 0>;
+// the balance ablations are built for hash_mode 0 only (checked by the parameter resolution)
+PackKernel pack_kernel(bool per_vertex, int hm, int bal = TC_BALANCE_VC) {
+    switch (bal) {
+        case TC_BALANCE_WC:
+            return per_vertex ? k_count_pack<true, 0, TC_BALANCE_WC> : k_count_pack<false, 0, TC_BALANCE_WC>;
+        case TC_BALANCE_SW8:
+            return per_vertex ? k_count_pack<true, 0, TC_BALANCE_SW8> : k_count_pack<false, 0, TC_BALANCE_SW8>;
+        case TC_BALANCE_SW16:
+            return per_vertex ? k_count_pack<true, 0, TC_BALANCE_SW16> : k_count_pack<false, 0, TC_BALANCE_SW16>;
+        case TC_BALANCE_PC:
+            return per_vertex ? k_count_pack<true, 0, TC_BALANCE_PC> : k_count_pack<false, 0, TC_BALANCE_PC>;
+        default:
+            break;
+    }
+    if (hm == 1) return per_vertex ? k_count_pack<true, 1, TC_BALANCE_VC> : k_count_pack<false, 1, TC_BALANCE_VC>;
+    return per_vertex ? k_count_pack<true, 0, TC_BALANCE_VC> : k_count_pack<false, 0, TC_BALANCE_VC>;
 }
 
 using BlockKernel = void (*)(const int32_t*, const int32_t*, const int2*, unsigned long long*, DevCounters*, int,
@@ -1126,6 +1253,10 @@ int lg2(int x) {
 
 }  // namespace
 
+size_t pc_scratch_bytes(const CountCfg& cfg) {
+    return (size_t)(cfg.warp_grid > 0 ? cfg.warp_grid : 1) * cfg.warps_per_block * PC_ROUND * sizeof(int2);
+}
+
 int pack_table_ints(int max_out_degree, int min_buckets) {
     int b = 2 * next_pow2(max_out_degree < 1 ? 1 : max_out_degree);
     if (b < min_buckets) b = min_buckets;
@@ -1152,8 +1283,8 @@ cudaError_t count_kernel_setup(CountCfg& cfg, int num_sms) {
     const int warp_smem = pack_smem_bytes(cfg);
     cudaError_t e = cudaSuccess;
     for (int pv = 0; pv < 2 && e == cudaSuccess; ++pv)
-        e = cudaFuncSetAttribute(pack_kernel(pv, cfg.hash_mode), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 warp_smem);
+        e = cudaFuncSetAttribute(pack_kernel(pv, cfg.hash_mode, cfg.balance),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(block_kernel(cfg.hash_mode), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              cfg.block_smem_bytes);
@@ -1161,7 +1292,7 @@ cudaError_t count_kernel_setup(CountCfg& cfg, int num_sms) {
     e = cudaFuncSetAttribute(edge_kernel(cfg.hash_mode), cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pack_kernel(false, cfg.hash_mode),
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pack_kernel(false, cfg.hash_mode, cfg.balance),
                                                       cfg.warps_per_block * 32,
                                                       warp_smem);
     if (e != cudaSuccess) return e;
@@ -1176,7 +1307,8 @@ cudaError_t count_kernel_setup(CountCfg& cfg, int num_sms) {
 cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t n, const int32_t* warp_list,
                          const int2* warp_desc, const int2* items, unsigned long long* per_vertex,
                          const CountCfg& cfg, DevCounters* ctr, cudaStream_t st, long long* launches,
-                         const int2* dag_bnd) {
+                         const int2* dag_bnd, int2* pc_scratch) {
+    if (cfg.balance == TC_BALANCE_PC && !pc_scratch) return cudaErrorInvalidValue;
     if (cfg.edge_centric) {
         *launches += 1;
         edge_kernel(cfg.hash_mode)<<<cfg.warp_grid, cfg.warps_per_block * 32, pack_smem_bytes(cfg), st>>>(
@@ -1190,10 +1322,10 @@ cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t
     block_kernel(cfg.hash_mode)<<<cfg.block_grid, cfg.block_threads, cfg.block_smem_bytes, st>>>(
         dag_ptr, dag_col, items, per_vertex, ctr, (int)n, table_off, count_block_part_max(cfg), cfg.item_neighbors,
         quad, cfg.cycle_timing, dag_bnd);
-    pack_kernel(per_vertex != nullptr, cfg.hash_mode)<<<cfg.warp_grid, cfg.warps_per_block * 32,
-                                                      pack_smem_bytes(cfg), st>>>(
+    pack_kernel(per_vertex != nullptr, cfg.hash_mode, cfg.balance)<<<cfg.warp_grid, cfg.warps_per_block * 32,
+                                                                   pack_smem_bytes(cfg), st>>>(
         dag_ptr, dag_col, warp_desc, warp_list, per_vertex, ctr, (int)n, cfg.warp_area_ints,
-        lg2(cfg.warp_min_buckets), cfg.chunk, quad, cfg.cycle_timing, dag_bnd);
+        lg2(cfg.warp_min_buckets), cfg.chunk, quad, cfg.cycle_timing, dag_bnd, pc_scratch);
     return cudaGetLastError();
 }
 

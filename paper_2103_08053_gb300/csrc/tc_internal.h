@@ -60,6 +60,7 @@ struct CountCfg {
     int quad_loads; // 1: warp workers read 2-hop lists as 16-byte quads (when dag_col is 16-byte aligned)
     int cycle_timing;  // 1: counting kernels add their build / probe cycles to DevCounters
     int edge_centric;  // 1: Algorithm 2 ablation (table of N+(u) rebuilt for every out-edge)
+    int balance;       // TC_BALANCE_*: how warp workers spread 2-hop lists over lanes (Sec. 4.2)
 };
 
 // One graph of an orientation pass. A batch places its graphs in one padded
@@ -125,7 +126,10 @@ cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, i
 cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t n, const int32_t* warp_list,
                          const int2* warp_desc, const int2* items, unsigned long long* per_vertex,
                          const CountCfg& cfg, DevCounters* ctr, cudaStream_t st, long long* launches,
-                         const int2* dag_bnd = nullptr);
+                         const int2* dag_bnd = nullptr, int2* pc_scratch = nullptr);
+// device bytes of the physical-combination scratch (cfg.balance == TC_BALANCE_PC): one
+// round of combined (key, table) pairs per warp of the warp-worker grid
+size_t pc_scratch_bytes(const CountCfg& cfg);
 int count_block_budget_ints(const CountCfg& cfg);
 int count_block_part_max(const CountCfg& cfg);
 // ints of one warp-worker table for out-degree d (2*nextpow2(d) buckets of 4 slots + byte lengths)

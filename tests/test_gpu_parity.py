@@ -173,6 +173,27 @@ def test_per_vertex_counts(ctx):
     d.free()
 
 
+@pytest.mark.parametrize("balance", [1, 2, 3, 4])
+def test_balance_modes_per_vertex_and_long_lists(T, balance):
+    # per-vertex counts under each Sec. 4.2 alternative, on graphs whose 2-hop
+    # lists are longer than a physical-combination round (stars joined to a
+    # clique: a warp vertex whose out-neighbours have d+ in the thousands)
+    hub = G.disjoint_union([G.complete(70), G.star(3000), G.rmat(12, 16, seed=21)])
+    big = G.from_edge_list(2600, [(a, b) for a in range(2400, 2600) for b in range(a + 1, 2600)] +
+                           [(a, b) for a in range(0, 2400) for b in range(2400, 2405)])
+    for g in (hub, big):
+        want_total, want_pv = oracle.count_dag(oracle.orient(g), per_vertex=True)
+        with T.Context(0, params=dict(balance=balance)) as c:
+            rp, col = dev(g)
+            d = c.orient(g.n, rp, col)
+            pv = torch.zeros(g.n, dtype=torch.int64, device="cuda")
+            assert c.count_dag(d, per_vertex=pv) == want_total
+            assert np.array_equal(pv.cpu().numpy().astype(np.uint64), want_pv)
+            d.free()
+            assert c.count(g.n, rp, col) == want_total
+            assert c.count_batch([(g.n, rp, col), (g.n, rp, col)]) == [want_total, want_total]
+
+
 def test_unaligned_dag_and_ragged_quads(ctx):
     # 16-byte quad loads need an aligned dag_col; a DAG whose dag_col starts 4
     # bytes past an alignment boundary is probed one key per lane. Both must
@@ -223,6 +244,13 @@ PARAM_SETS = {
     "scalar_loads": dict(scalar_loads=1),                      # one 2-hop key per lane per load
     "edge_centric": dict(edge_centric=1),                      # Algorithm 2 ablation: a table per out-edge
     "cycle_timing": dict(record_timing=2),
+    # Sec. 4.2's alternatives to virtual combination (warp workers)
+    "balance_wc": dict(balance=1),
+    "balance_sw8": dict(balance=2),
+    "balance_sw16": dict(balance=3),
+    "balance_pc": dict(balance=4),
+    "balance_pc_small_packs": dict(balance=4, warp_max_out_degree=12, warp_area_ints=144, chunk=7),
+    "balance_sw8_all_warp": dict(balance=2, warp_max_out_degree=255, warp_area_ints=2304, warps_per_block=4),
 }
 
 
@@ -336,7 +364,8 @@ def test_asymmetric_input_does_not_overflow(T, ctx):
 def test_invalid_params(T):
     for bad in (dict(warp_min_buckets=48), dict(item_neighbors=2048), dict(shard_count=2, shard_index=2),
                 dict(warp_max_out_degree=256), dict(block_threads=100), dict(chunk=33), dict(warp_area_ints=320),
-                dict(warp_min_buckets=8), dict(hash_mode=2)):
+                dict(warp_min_buckets=8), dict(hash_mode=2), dict(balance=5), dict(balance=-1),
+                dict(balance=1, hash_mode=1)):
         with pytest.raises(T.TcError) as ei:
             T.Context(0, params=bad)
         assert ei.value.status == T.TC_ERR_INVALID_ARG
