@@ -124,6 +124,15 @@ typedef struct {
                                     of the alternatives the paper compares it with. Same counts in every
                                     mode. The alternatives need hash_mode 0 and apply to the warp
                                     workers; thread-block workers always use virtual combination. */
+    int32_t warp_order;          /* order in which warp workers take their vertices: 0 auto (1 for
+                                    graphs of at least 2^24 adjacency entries, else 2); 1 grouped by the
+                                    key min(u, first neighbour of u) -- with rows sorted by id, the
+                                    smallest id of the closed neighbourhood {u} + N(u), a min-hash of
+                                    N(u) -- so that vertices with overlapping neighbourhoods are counted
+                                    together and share the 2-hop lists they read in L2 (unsorted rows
+                                    give an arbitrary order); 2 vertex order. Same counts in every mode.
+                                    Single-graph calls on a CSR with fewer than 2^31 entries (tc_count,
+                                    tc_count_async, tc_count_host); batches use vertex order. */
 } tc_params;
 
 /* tc_params.balance (Sec. 4.2's intra-vertex workload balancing methods) */

@@ -63,7 +63,8 @@ class tc_params(ctypes.Structure):
                 ("item_neighbors", c_int32), ("chunk", c_int32), ("warps_per_block", c_int32),
                 ("shard_count", c_int32), ("shard_index", c_int32), ("validate", c_int32),
                 ("record_timing", c_int32), ("hash_mode", c_int32), ("scalar_loads", c_int32),
-                ("edge_centric", c_int32), ("balance", c_int32)]
+                ("edge_centric", c_int32), ("balance", c_int32),
+                ("warp_order", c_int32)]
 
 
 class tc_timing(ctypes.Structure):

@@ -129,6 +129,7 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         p.scalar_loads = in->scalar_loads;
         p.edge_centric = in->edge_centric;
         p.balance = in->balance;
+        p.warp_order = in->warp_order;
 #undef TAKE
     }
     if (p.warp_max_out_degree < 1 || p.warp_max_out_degree > 255)
@@ -159,6 +160,8 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "balance must be one of TC_BALANCE_VC .. TC_BALANCE_PC");
     if (p.balance != TC_BALANCE_VC && p.hash_mode != 0)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "the balance ablation modes use hash_mode 0");
+    if (p.warp_order < 0 || p.warp_order > 2)
+        return ctx_fail(ctx, TC_ERR_INVALID_ARG, "warp_order must be 0, 1 or 2");
     if (p.record_timing < 0 || p.record_timing > 2)
         return ctx_fail(ctx, TC_ERR_INVALID_ARG, "record_timing must be 0, 1 or 2");
     if (p.chunk < 1 || p.chunk > 32) return ctx_fail(ctx, TC_ERR_INVALID_ARG, "chunk must be in [1, 32]");
@@ -191,6 +194,7 @@ tc_status tcg::resolve_params(tc_ctx* ctx, const tc_params* in, tc_params* out, 
         cfg->cycle_timing = p.record_timing == 2 ? 1 : 0;
         cfg->edge_centric = p.edge_centric;
         cfg->balance = p.balance;
+        cfg->warp_order = p.warp_order;
         cfg->warp_grid = cfg->block_grid = 0;
     }
     return TC_OK;
@@ -275,7 +279,8 @@ static tc_status enqueue_orient(tc_ctx* ctx, Workspace& ws, const tc_csr* g, int
 // entries the input allows (nullptr / -1 for a compact DAG).
 static tc_status enqueue_count(tc_ctx* ctx, Workspace& ws, const int32_t* dag_ptr, const int32_t* dag_col,
                                int64_t n, uint64_t* per_vertex, cudaStream_t st, TimedCall* tm,
-                               const int2* dag_bnd = nullptr, long long max_m = -1) {
+                               const int2* dag_bnd = nullptr, long long max_m = -1,
+                               const int32_t* ncol = nullptr) {
     DevCounters* ctr = (DevCounters*)ws.ctr.p;
     cudaError_t e = cudaSuccess;
     long long nl = 0;
@@ -283,7 +288,8 @@ static tc_status enqueue_count(tc_ctx* ctx, Workspace& ws, const int32_t* dag_pt
     if (e == cudaSuccess && n > 0) {
         const int64_t m_cap = ws.items.bytes / sizeof(int2);
         e = launch_bin(dag_ptr, n, ctx->cfg, (int32_t*)ws.warp_list.p, (int2*)ws.warp_desc.p, (int2*)ws.items.p,
-                       m_cap, ctr, ctx->num_sms, st, &nl, dag_bnd, max_m);
+                       m_cap, ctr, ctx->num_sms, st, &nl, dag_bnd, max_m, ncol, (int32_t*)ws.okey.p,
+                       (int32_t*)ws.ohist.p, (long long*)ws.partial.p);
         timing_mark(tm, 2, st);
         if (e == cudaSuccess)
             e = launch_count(dag_ptr, dag_col, n, (const int32_t*)ws.warp_list.p, (const int2*)ws.warp_desc.p,
@@ -295,6 +301,21 @@ static tc_status enqueue_count(tc_ctx* ctx, Workspace& ws, const int32_t* dag_pt
     timing_mark(tm, 3, st);
     ctx->launches += nl;
     return cuda_status(ctx, e, "counting kernels");
+}
+
+// The ordered warp list (tc_params.warp_order) for a row-local count of a
+// graph with nnz adjacency entries in col: col when the order applies (the
+// key and histogram arrays ensured), else null.
+static tc_status order_keys(tc_ctx* ctx, Workspace& ws, int64_t n, int64_t nnz, const int32_t* col,
+                            cudaStream_t st, const int32_t** ncol) {
+    *ncol = nullptr;
+    const int mode = ctx->cfg.warp_order;
+    if (n <= 0 || mode == 2 || (mode == 0 && nnz < (1LL << 24))) return TC_OK;
+    tc_status s;
+    if ((s = ws.okey.ensure(ctx, (size_t)(n + 1) * 4, st))) return s;
+    if ((s = ws.ohist.ensure(ctx, (size_t)(n + 1) * 4, st))) return s;
+    *ncol = col;
+    return TC_OK;
 }
 
 // Read the 64-byte counters back (blocking) and map error bits.
@@ -509,9 +530,11 @@ tc_status tc_count_async(tc_ctx* ctx, const tc_csr* g, uint64_t* count_device, i
     // row-local DAG (the oriented lists left in the CSR's row slots: no scan,
     // no compaction) whenever the offsets fit int32; else the compact DAG
     const bool row_local = g->nnz < 0x7fffffffLL && !ctx->cfg.edge_centric;
+    const int32_t* ncol = nullptr;
     if (row_local) {
         if ((s = ws.bnd.ensure(ctx, (size_t)(g->n + 1) * 8, st))) return s;
         if ((s = ws.dag_col.ensure(ctx, (size_t)(g->nnz + 1) * 4, st))) return s;
+        if ((s = order_keys(ctx, ws, g->n, g->nnz, g->col, st, &ncol))) return s;
     } else if ((s = ws.dag_col.ensure(ctx, (size_t)(g->nnz / 2 + 1) * 4, st))) {
         return s;
     }
@@ -531,7 +554,7 @@ tc_status tc_count_async(tc_ctx* ctx, const tc_csr* g, uint64_t* count_device, i
         timing_mark(tm, 1, st);
         if (!s)
             s = enqueue_count(ctx, ws, nullptr, (int32_t*)ws.dag_col.p, g->n, nullptr, st, tm, (int2*)ws.bnd.p,
-                              g->nnz / 2);
+                              g->nnz / 2, ncol);
     } else {
         if (!s) s = enqueue_orient(ctx, ws, g, (int32_t*)ws.dag_ptr.p, (int32_t*)ws.dag_col.p, g->nnz / 2 + 1, st);
         timing_mark(tm, 1, st);
@@ -589,6 +612,8 @@ static tc_status count_host_pieces(tc_ctx* ctx, const tc_csr* g, uint64_t* count
     if ((s = ensure_orient_ws(ctx, ws, n, nnz, st))) return s;
     if ((s = ws.bnd.ensure(ctx, (size_t)(n + 1) * 8, st))) return s;
     if ((s = ws.dag_col.ensure(ctx, (size_t)(nnz + 1) * 4, st))) return s;
+    const int32_t* ncol = nullptr;
+    if ((s = order_keys(ctx, ws, n, nnz, (const int32_t*)ctx->csr_copy.b.p, st, &ncol))) return s;
     if (!ctx->aux_stream) {
         s = cuda_status(ctx, cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking), "cudaStreamCreate");
         for (cudaEvent_t& e : ctx->aux_ev)
@@ -642,7 +667,8 @@ static tc_status count_host_pieces(tc_ctx* ctx, const tc_csr* g, uint64_t* count
     }
     timing_mark(tm, 1, st);
     if (!s)
-        s = enqueue_count(ctx, ws, nullptr, (int32_t*)ws.dag_col.p, n, nullptr, st, tm, (int2*)ws.bnd.p, nnz / 2);
+        s = enqueue_count(ctx, ws, nullptr, (int32_t*)ws.dag_col.p, n, nullptr, st, tm, (int2*)ws.bnd.p, nnz / 2,
+                          ncol);
     uint64_t* d_count = (uint64_t*)ctx->out_scalars.p;
     int32_t* d_err = (int32_t*)((char*)ctx->out_scalars.p + 8);
     if (!s) {

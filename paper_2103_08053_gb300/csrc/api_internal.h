@@ -28,9 +28,10 @@ struct DevBuf {
 struct Workspace {
     DevBuf deg, kept, partial, dag_ptr, dag_col, warp_list, warp_desc, items, ctr, stats, hubs, kbits, bnd;
     DevBuf pc;  // physical-combination scratch (tc_params.balance == TC_BALANCE_PC only)
+    DevBuf okey, ohist;  // ordered warp list: per-vertex locality keys, key histogram / offsets
     void release_all(tc_ctx* ctx) {
         for (DevBuf* b : {&deg, &kept, &partial, &dag_ptr, &dag_col, &warp_list, &warp_desc, &items, &ctr, &stats,
-                          &hubs, &kbits, &bnd, &pc})
+                          &hubs, &kbits, &bnd, &pc, &okey, &ohist})
             b->release(ctx);
     }
 };

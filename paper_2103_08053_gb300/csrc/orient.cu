@@ -518,8 +518,11 @@ __global__ void __launch_bounds__(SCAN_THREADS)
     if (threadIdx.x == 0) partial[blockIdx.x] = tot;
 }
 
+// to_warp_count: the scan is of the ordered warp list's key histogram, whose
+// total is the warp list's length (else the DAG offsets: total = m).
 __global__ void __launch_bounds__(SCAN_TOP_THREADS)
-    k_scan_top(long long* __restrict__ partial, int nb, int32_t* __restrict__ out, int64_t n, DevCounters* ctr) {
+    k_scan_top(long long* __restrict__ partial, int nb, int32_t* __restrict__ out, int64_t n, DevCounters* ctr,
+               int to_warp_count) {
     __shared__ long long sh[33];
     const int per = (nb + SCAN_TOP_THREADS - 1) / SCAN_TOP_THREADS;
     const int b0 = threadIdx.x * per, b1 = min(nb, b0 + per);
@@ -533,9 +536,13 @@ __global__ void __launch_bounds__(SCAN_TOP_THREADS)
         pre += x;
     }
     if (threadIdx.x == 0) {
-        ctr->m = tot;
-        if (tot > 0x7fffffffLL) atomicOr(&ctr->err, ERRBIT_DAG_TOO_BIG);
-        out[n] = (int32_t)tot;
+        if (to_warp_count) {
+            ctr->n_warp = (int)tot;  // <= n < 2^31
+        } else {
+            ctr->m = tot;
+            if (tot > 0x7fffffffLL) atomicOr(&ctr->err, ERRBIT_DAG_TOO_BIG);
+            out[n] = (int32_t)tot;
+        }
     }
 }
 
@@ -571,9 +578,16 @@ __global__ void __launch_bounds__(SCAN_THREADS)
 
 // ---- binning ----------------------------------------------------------------
 
+// ncol != nullptr (ordered warp list; ncol: the input CSR's neighbour ids,
+// whose rows start where the row-local DAG's do): instead of appending a
+// warp-class vertex to the warp list, give it the locality key min(u, first
+// neighbour of u) -- the smallest id of the closed neighbourhood {u} + N(u)
+// when rows are sorted, a min-hash of N(u) -- in okey[u] and count it in
+// ohist[key]; k_place then lays the list out in key order.
 __global__ void k_bin(const int32_t* __restrict__ dag_ptr, const int2* __restrict__ dag_bnd, int64_t n,
                       int warp_max, int item_nbrs, int shard_count, int shard_index, int32_t* __restrict__ warp_list,
                       int2* __restrict__ warp_desc, int2* __restrict__ items, int64_t item_cap, long long max_m,
+                      const int32_t* __restrict__ ncol, int32_t* __restrict__ okey, int32_t* __restrict__ ohist,
                       DevCounters* ctr) {
     if (ctr->err) return;
     if (max_m >= 0 && ctr->m > max_m) {  // more kept entries than an undirected CSR can give
@@ -596,8 +610,14 @@ __global__ void k_bin(const int32_t* __restrict__ dag_ptr, const int2* __restric
             }
         }
         const bool is_warp = d >= 2 && d <= warp_max;
-        const unsigned wm = __ballot_sync(FULL, is_warp);
-        if (wm) {
+        if (ncol) {
+            if (is_warp) {  // d+ >= 2: the row is not empty
+                const int c = __ldg(ncol + a);
+                const int key = ((unsigned)c < (unsigned long long)u) ? c : (int)u;
+                okey[u] = key;
+                atomicAdd(&ohist[key], 1);
+            }
+        } else if (const unsigned wm = __ballot_sync(FULL, is_warp)) {
             const int leader = __ffs(wm) - 1;
             int pos = 0;
             if (lane == leader) pos = atomicAdd(&ctr->n_warp, __popc(wm));
@@ -617,6 +637,27 @@ __global__ void k_bin(const int32_t* __restrict__ dag_ptr, const int2* __restric
             } else {
                 atomicOr(&ctr->err, ERRBIT_DAG_OVERFLOW);
             }
+        }
+    }
+}
+
+// Ordered warp list, second pass: every warp-class vertex takes the next slot
+// of its key's run (ohist: the runs' exclusive offsets after the scan), so
+// vertices with the same key sit next to each other in the list and are
+// counted at about the same time; their out-neighbours overlap, so the 2-hop
+// lists they read are shared in L2. The order within a run is arbitrary.
+__global__ void k_place(const int2* __restrict__ dag_bnd, int64_t n, int warp_max, int shard_count, int shard_index,
+                        const int32_t* __restrict__ okey, int32_t* __restrict__ ohist, int32_t* __restrict__ warp_list,
+                        int2* __restrict__ warp_desc, DevCounters* ctr) {
+    if (ctr->err) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
+        if (shard_count > 1 && (int)(u % shard_count) != shard_index) continue;
+        const int2 b = dag_bnd[u];
+        if (b.y >= 2 && b.y <= warp_max) {
+            const int pos = atomicAdd(&ohist[okey[u]], 1);
+            warp_list[pos] = (int32_t)u;
+            warp_desc[pos] = b;
         }
     }
 }
@@ -648,7 +689,7 @@ cudaError_t orient_t(const GraphRef& one, const GraphRef* gs, int k, int64_t tot
     if (rdag) return cudaGetLastError();  // row-local DAG: bnd and rdag are the DAG
     const int nb = scan_blocks(total);
     k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(kept, total, partial);
-    k_scan_top<<<1, SCAN_TOP_THREADS, 0, st>>>(partial, nb, dag_ptr, total, ctr);
+    k_scan_top<<<1, SCAN_TOP_THREADS, 0, st>>>(partial, nb, dag_ptr, total, ctr, 0);
     k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(kept, total, partial, dag_ptr);
     k_orient<Off, true, BATCH><<<og, ORIENT_THREADS, 0, st>>>(one, gs, k, total, deg, nullptr, dag_ptr, dag_col,
                                                                dag_cap, kbits, nullptr, nullptr, 0, groups, ctr);
@@ -727,13 +768,27 @@ cudaError_t launch_orient_row_local_pieces(const void* row_ptr, int offset_bits,
 
 cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* warp_desc,
                        int2* items, int64_t item_cap, DevCounters* ctr, int num_sms, cudaStream_t st,
-                       long long* launches, const int2* dag_bnd, long long max_m) {
+                       long long* launches, const int2* dag_bnd, long long max_m, const int32_t* ncol,
+                       int32_t* okey, int32_t* ohist, long long* partial) {
     if (n <= 0) return cudaSuccess;
-    *launches += 1;
+    if (!dag_bnd || !ncol) okey = nullptr;
     int g = (int)((n + 255) / 256);
     if (g > num_sms * 16) g = num_sms * 16;
+    if (okey) {
+        const cudaError_t e = cudaMemsetAsync(ohist, 0, (size_t)n * 4, st);
+        if (e != cudaSuccess) return e;
+    }
+    *launches += okey ? 5 : 1;
     k_bin<<<g, 256, 0, st>>>(dag_ptr, dag_bnd, n, cfg.warp_max_out_degree, cfg.item_neighbors, cfg.shard_count,
-                             cfg.shard_index, warp_list, warp_desc, items, item_cap, max_m, ctr);
+                             cfg.shard_index, warp_list, warp_desc, items, item_cap, max_m, okey ? ncol : nullptr,
+                             okey, ohist, ctr);
+    if (!okey) return cudaGetLastError();
+    const int nb = scan_blocks(n);
+    k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(ohist, n, partial);
+    k_scan_top<<<1, SCAN_TOP_THREADS, 0, st>>>(partial, nb, ohist, n, ctr, 1);
+    k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(ohist, n, partial, ohist);
+    k_place<<<g, 256, 0, st>>>(dag_bnd, n, cfg.warp_max_out_degree, cfg.shard_count, cfg.shard_index, okey, ohist,
+                               warp_list, warp_desc, ctr);
     return cudaGetLastError();
 }
 

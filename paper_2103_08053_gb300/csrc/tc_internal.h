@@ -61,6 +61,7 @@ struct CountCfg {
     int cycle_timing;  // 1: counting kernels add their build / probe cycles to DevCounters
     int edge_centric;  // 1: Algorithm 2 ablation (table of N+(u) rebuilt for every out-edge)
     int balance;       // TC_BALANCE_*: how warp workers spread 2-hop lists over lanes (Sec. 4.2)
+    int warp_order;    // 0 auto, 1 warp list grouped by locality key, 2 vertex order
 };
 
 // One graph of an orientation pass. A batch places its graphs in one padded
@@ -117,10 +118,16 @@ cudaError_t launch_orient_batch(const GraphRef* graphs, int k, int offset_bits, 
                                 int2* bnd = nullptr, int32_t* rdag = nullptr, long long entries = 0);
 
 // Binning (Sec. 4.3) from an existing DAG: fills warp_list / items / counters.
+// ncol (the input CSR's neighbour ids; row-local DAG of one graph only; okey,
+// ohist: n ints, partial: scan_blocks(n) + 2 long longs): the warp list is
+// laid out in the order of a locality key, min(u, first neighbour of u) --
+// a histogram of the keys, its scan, and a placement pass -- instead of in
+// vertex order.
 cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* warp_desc,
                        int2* items, int64_t item_cap, DevCounters* ctr, int num_sms, cudaStream_t st,
                        long long* launches,
-                       const int2* dag_bnd = nullptr, long long max_m = -1);
+                       const int2* dag_bnd = nullptr, long long max_m = -1, const int32_t* ncol = nullptr,
+                       int32_t* okey = nullptr, int32_t* ohist = nullptr, long long* partial = nullptr);
 
 // ---- counting (count.cu) ----------------------------------------------------
 cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t n, const int32_t* warp_list,

@@ -251,6 +251,10 @@ PARAM_SETS = {
     "balance_pc": dict(balance=4),
     "balance_pc_small_packs": dict(balance=4, warp_max_out_degree=12, warp_area_ints=144, chunk=7),
     "balance_sw8_all_warp": dict(balance=2, warp_max_out_degree=255, warp_area_ints=2304, warps_per_block=4),
+    # warp list grouped by the min-hash locality key (auto turns it on for >= 2^24 entries only)
+    "warp_order_keys": dict(warp_order=1),
+    "warp_order_keys_small_packs": dict(warp_order=1, warp_max_out_degree=12, warp_area_ints=144, chunk=7),
+    "warp_order_vertex": dict(warp_order=2),
 }
 
 
@@ -285,14 +289,37 @@ def test_adversarial_overflow(T, k, params, hash_mode):
         assert gpu_count(c, g) == want
 
 
-def test_shards_sum_to_total(T):
+@pytest.mark.parametrize("warp_order", [0, 1])
+def test_shards_sum_to_total(T, warp_order):
     g = G.rmat(13, 16, seed=15)
     want = oracle.count(g)
     parts = []
     for i in range(3):
-        with T.Context(0, params=dict(shard_count=3, shard_index=i)) as c:
+        with T.Context(0, params=dict(shard_count=3, shard_index=i, warp_order=warp_order)) as c:
             parts.append(gpu_count(c, g))
     assert sum(parts) == want and all(p > 0 for p in parts)
+
+
+def test_ordered_warp_list_launches_and_host_pieces(T):
+    # warp_order 1: binning gives every warp-class vertex a locality key and
+    # becomes histogram + 3 scan kernels + placement (4 more launches); the
+    # piecewise host path (>= 2^20 entries) takes the same order
+    g = G.rmat(13, 16, seed=20)
+    big = G.disjoint_union([G.rgg(30_001, 40.0, seed=35), G.star(5000), G.wheel(700),
+                            G.rmat(14, 16, seed=36), G.complete(45)])
+    with T.Context(0, params=dict(warp_order=1)) as c:
+        rp, col = dev(g)
+        l0 = c.kernel_launches()
+        assert c.count(g.n, rp, col) == oracle.count(g)
+        assert c.kernel_launches() - l0 == 11
+        assert gpu_count(c, G.shuffle_rows(g, 3)) == oracle.count(g)   # unsorted rows: an arbitrary order
+        want = oracle.count(big)
+        for bits in (32, 64):
+            rph = np.ascontiguousarray(big.row_ptr.astype(np.int64 if bits == 64 else np.int32))
+            colh = np.ascontiguousarray(big.col, dtype=np.int32)
+            assert c.count_host(big.n, rph, colh) == want
+            assert c.count_host(big.n, torch.from_numpy(rph).pin_memory().numpy(),
+                                torch.from_numpy(colh).pin_memory().numpy()) == want
 
 
 # ------------------------------------------------------------ entry points
@@ -365,7 +392,7 @@ def test_invalid_params(T):
     for bad in (dict(warp_min_buckets=48), dict(item_neighbors=2048), dict(shard_count=2, shard_index=2),
                 dict(warp_max_out_degree=256), dict(block_threads=100), dict(chunk=33), dict(warp_area_ints=320),
                 dict(warp_min_buckets=8), dict(hash_mode=2), dict(balance=5), dict(balance=-1),
-                dict(balance=1, hash_mode=1)):
+                dict(balance=1, hash_mode=1), dict(warp_order=3), dict(warp_order=-1)):
         with pytest.raises(T.TcError) as ei:
             T.Context(0, params=bad)
         assert ei.value.status == T.TC_ERR_INVALID_ARG
