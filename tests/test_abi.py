@@ -42,6 +42,18 @@ def test_default_params(tc):
     assert p["warp_min_buckets"] & (p["warp_min_buckets"] - 1) == 0
     assert p["item_neighbors"] <= p["block_threads"]
     assert p["shard_count"] == 1 and p["shard_index"] == 0
+    assert p["balance"] == T.TC_BALANCE_VC == 0 and p["warp_order"] == 0
+    assert (T.TC_BALANCE_WC, T.TC_BALANCE_SW8, T.TC_BALANCE_SW16, T.TC_BALANCE_PC) == (1, 2, 3, 4)
+
+
+def test_params_struct_matches_header(tc):
+    # the ctypes mirror of tc_params has the header's fields, in order
+    import re
+    hdr = open(os.path.join(ROOT, "include", "tc.h")).read()
+    end = hdr.index("} tc_params;")
+    body = hdr[hdr.rindex("typedef struct", 0, end):end]
+    fields = re.findall(r"int32_t\s+(\w+)(?:\[\d+\])?;", body)
+    assert fields == [f for f, _ in tc.tc_params._fields_]
 
 
 def test_null_arguments_rejected_without_gpu(tc):
