@@ -290,7 +290,10 @@ def measure_reorder(T, torch, dev, graphs):
     """Sec. 4.1 study: for each graph, tc_reorder by in-degree and by
     collective out-degree; the max collision and Eq. 2 cost of 32-bucket
     tables (x mod 32 and multiplicative), and the counting time under both
-    table hashes, before and after reordering. The count must not change."""
+    table hashes with the warp workers in vertex order (as the paper's queue
+    hands them out), and with the library's defaults (the ordered warp list
+    on graphs of >= 2^24 entries), before and after reordering. The count
+    must not change."""
     rows = []
     for name, (n, rp, col) in graphs.items():
         with T.Context(dev.index) as c:
@@ -309,8 +312,10 @@ def measure_reorder(T, torch, dev, graphs):
                 row = {"graph": name, "order": label, "reorder_ms": ms_re,
                        "max_collision_mod32": st["max_collision_mod32"], "phi_mod32": st["phi_mod32"],
                        "max_collision_mult32": st["max_collision_mult32"], "phi_mult32": st["phi_mult32"]}
-                for hm, key in ((0, "count_ms_mult_hash"), (1, "count_ms_mod_hash")):
-                    with T.Context(dev.index, params=dict(hash_mode=hm)) as ch:
+                for prm, key in ((dict(warp_order=2), "count_ms_mult_hash"),
+                                 (dict(warp_order=2, hash_mode=1), "count_ms_mod_hash"),
+                                 ({}, "count_ms_defaults")):
+                    with T.Context(dev.index, params=prm) as ch:
                         ms, tri = time_count(ch, torch, dev, n, r, cc)
                     row[key] = ms
                     base = tri if base is None else base
@@ -352,6 +357,39 @@ def measure_ablation(T, torch, dev, graphs):
                          "build_share": t["build_cycles"] / cyc if cyc else None,
                          "count_equal": tri == base == tri2})
     return rows
+
+
+def reorder_profile_run(args):
+    """The launch sequence for profiling Sec. 4.1's reorderings with ncu: one
+    graph, and for each order (none, in-degree, collective out-degree) one
+    tc_count with the warp workers in vertex order, so that k_count_pack runs
+    exactly three times, in that order. Prints one JSON line describing them
+    (an ncu run over this command captures the counters: shared-load
+    instructions, their bank conflicts, the L2 hit rate)."""
+    import numpy as np
+    import torch
+
+    import graphgen as G
+    import paper_2103_08053_gb300 as T
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    g = G.workload(args.reorder_profile)
+    n = g.n
+    rp = torch.from_numpy(g.row_ptr.astype(np.int32)).to(dev)
+    col = torch.from_numpy(np.ascontiguousarray(g.col, dtype=np.int32)).to(dev)
+    rows = []
+    with T.Context(0, params=dict(warp_order=2, hash_mode=args.profile_hash_mode)) as c:
+        for kind, label in ((None, "none"), (T.TC_REORDER_INDEGREE, "indegree"),
+                            (T.TC_REORDER_COLLECTIVE, "collective")):
+            r, cc = (rp, col) if kind is None else c.reorder(n, rp, col, kind, relabel=True)[1:]
+            d = c.orient(n, r, cc)
+            st = c.dag_stats(d)
+            d.free()
+            rows.append({"order": label, "triangles": c.count(n, r, cc),
+                         "max_collision_mod32": st["max_collision_mod32"],
+                         "max_collision_mult32": st["max_collision_mult32"]})
+    print(json.dumps({"reorder_profile": args.reorder_profile, "hash_mode": args.profile_hash_mode, "n": n, "m": g.m,
+                      "k_count_pack_launches": [r["order"] for r in rows], "rows": rows}), flush=True)
 
 
 # -------------------------------------------------------------- the arms
@@ -492,7 +530,8 @@ def run_gb300(args):
                      "bytes_model": "4(n+1) + 12m + 4W+"},
         "e2e": {"value": g.m / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(rp_h.nbytes + col_h.nbytes), "d2h_bytes_per_step": 16,
-                "h2d_copy_ms": h2d_ms, "api": "tc_count_host (pinned host CSR)"},
+                "h2d_copy_ms": h2d_ms, "host_pinned": bool(col_pin.is_pinned()),
+                "api": "tc_count_host (pinned host CSR)"},
         "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -579,7 +618,14 @@ def main():
                     help="1: also run the Sec. 4.1 reordering study (rank 0)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="seconds of Poisson arrivals for the serving measurement (0: skip; the config is 60)")
+    ap.add_argument("--reorder-profile", default=None, metavar="GRAPH",
+                    help="only run the Sec. 4.1 profiling sequence on this workload (e.g. rgg20, rmat21) and exit")
+    ap.add_argument("--profile-hash-mode", type=int, choices=[0, 1], default=0,
+                    help="table hash of the profiling sequence: 0 multiplicative (default), 1 x mod B (Algorithm 1)")
     args = ap.parse_args()
+    if args.reorder_profile:
+        reorder_profile_run(args)
+        return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.workload != "rgg22":
