@@ -170,6 +170,7 @@ tc_status BatchRunner::enqueue(tc_ctx* ctx) {
                        (int2*)ws.items.p, (int64_t)(ws.items.bytes / sizeof(int2)), ctr, ctx->num_sms, stream,
                        &nl, bnd, row_local ? nnz_total / 2 : -1);
     CountCfg cfg = ctx->cfg;
+    cfg.pop_contiguous = 1;  // warps on a few graphs at a time: their lists stay in L2
     if (grid_share < 1.0f) {  // leave SMs to runners on other streams
         cfg.warp_grid = cfg.warp_grid * grid_share < 1.0f ? 1 : (int)(cfg.warp_grid * grid_share);
         cfg.block_grid = cfg.block_grid * grid_share < 1.0f ? 1 : (int)(cfg.block_grid * grid_share);

@@ -74,9 +74,6 @@ static_assert(VC_UNROLL == 4, "the bitmap owner path reads four window words at 
 #ifndef BLOCK_ADAPTIVE_PIECE
 #define BLOCK_ADAPTIVE_PIECE 1  // 1: pieces sized so that each warp of the block gets about two
 #endif
-#ifndef PACK_STRIDED
-#define PACK_STRIDED 1  // 1: a pop takes warp-list entries S apart (see k_count_pack)
-#endif
 #ifndef BLOCK_SLOTS
 #define BLOCK_SLOTS 4  // slots per bucket of the thread-block tables (2: overflow chains at load 1/2 cost more)
 #endif
@@ -432,6 +429,10 @@ __device__ __forceinline__ uint32_t vc_pack_quad(int s, int l, int td, const int
     }
     const int4* __restrict__ quads = reinterpret_cast<const int4*>(dag_col);
     int cum = 0;
+    // per-vertex hits (SLOT_HITS): a lane's quads come from lists in list
+    // order, so its pack slot only grows; hits are summed per run of one slot
+    // and added to the slot's counter when the run ends
+    int run_slot = 0, run_hits = 0;
     for (int base = 0; base < total; base += 32 * QUAD_UNROLL) {
         int4 v[QUAD_UNROLL];
         int lo[QUAD_UNROLL], hi[QUAD_UNROLL], kd[QUAD_UNROLL];
@@ -484,9 +485,18 @@ __device__ __forceinline__ uint32_t vc_pack_quad(int s, int l, int td, const int
                 }
             }
             hits += hq;
-            if (SLOT_HITS && hq) atomicAdd(&stage[128 + ((kd[q] >> 21) & 31)], hq);
+            if (SLOT_HITS) {
+                const int sl = (kd[q] >> 21) & 31;
+                if (sl != run_slot) {
+                    if (run_hits) atomicAdd(&stage[128 + run_slot], run_hits);
+                    run_slot = sl;
+                    run_hits = 0;
+                }
+                run_hits += hq;
+            }
         }
     }
+    if (SLOT_HITS && run_hits) atomicAdd(&stage[128 + run_slot], run_hits);
     return hits;
 }
 
@@ -734,7 +744,7 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
                  const int2* __restrict__ desc, const int32_t* __restrict__ warp_list,
                  unsigned long long* __restrict__ per_vertex, DevCounters* ctr, int n, int area_ints,
                  int lg_min_buckets, int pop, int quad, int timing, const int2* __restrict__ dag_bnd,
-                 int2* __restrict__ pc_buf) {
+                 int2* __restrict__ pc_buf, int strided) {
     extern __shared__ int smem[];
     if (ctr->err) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -747,10 +757,11 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
     unsigned long long acc = 0;
     // A pop takes up to `pop` vertices of the warp list, fewer when the list
     // is short, so that there are at least 4 pops per warp of the grid.
-    // PACK_STRIDED: pop q takes entries q, q + S, q + 2S, ... (S =
-    // ceil(nlist / pop)), so every pop is a sample of the whole list and pops
-    // cost about the same even when vertex cost follows the list order (R-MAT
-    // ids: the heaviest vertices first).
+    // strided: pop q takes entries q, q + S, q + 2S, ... (S = ceil(nlist /
+    // pop)), so every pop is a sample of the whole list and pops cost about
+    // the same even when vertex cost follows the list order (R-MAT ids: the
+    // heaviest vertices first); else pops take consecutive entries (a batch:
+    // the warps then work on a few graphs at a time, whose lists stay in L2).
     {
         const int per = nlist / (4 * (int)(gridDim.x * (blockDim.x >> 5)));
         pop = per < 1 ? 1 : (per < pop ? per : pop);
@@ -758,11 +769,11 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
     const int S = (nlist + pop - 1) / pop;
     for (;;) {
         int i0 = 0;
-        if (lane == 0) i0 = atomicAdd(&ctr->q_warp, PACK_STRIDED ? 1 : pop);
+        if (lane == 0) i0 = atomicAdd(&ctr->q_warp, strided ? 1 : pop);
         i0 = __shfl_sync(FULL, i0, 0);
-        if (PACK_STRIDED ? i0 >= S : i0 >= nlist) break;
-        const int cnt = PACK_STRIDED ? min(pop, (nlist - i0 + S - 1) / S) : min(pop, nlist - i0);
-        const int li = PACK_STRIDED ? i0 + lane * S : i0 + lane;  // this lane's warp-list entry
+        if (strided ? i0 >= S : i0 >= nlist) break;
+        const int cnt = strided ? min(pop, (nlist - i0 + S - 1) / S) : min(pop, nlist - i0);
+        const int li = strided ? i0 + lane * S : i0 + lane;  // this lane's warp-list entry
         int a = 0, k = 0;
         if (lane < cnt) {
             const int2 d = __ldg(desc + li);
@@ -1202,7 +1213,7 @@ __global__ void __launch_bounds__(256) k_collision(const int32_t* __restrict__ d
 int pack_smem_bytes(const CountCfg& cfg) { return cfg.warps_per_block * (cfg.warp_area_ints + STAGE_INTS) * 4; }
 
 using PackKernel = void (*)(const int32_t*, const int32_t*, const int2*, const int32_t*, unsigned long long*,
-                            DevCounters*, int, int, int, int, int, int, const int2*, int2*);
+                            DevCounters*, int, int, int, int, int, int, const int2*, int2*, int);
 
 // the balance ablations are built for hash_mode 0 only (checked by the parameter resolution)
 PackKernel pack_kernel(bool per_vertex, int hm, int bal = TC_BALANCE_VC) {
@@ -1325,7 +1336,8 @@ cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t
     pack_kernel(per_vertex != nullptr, cfg.hash_mode, cfg.balance)<<<cfg.warp_grid, cfg.warps_per_block * 32,
                                                                    pack_smem_bytes(cfg), st>>>(
         dag_ptr, dag_col, warp_desc, warp_list, per_vertex, ctr, (int)n, cfg.warp_area_ints,
-        lg2(cfg.warp_min_buckets), cfg.chunk, quad, cfg.cycle_timing, dag_bnd, pc_scratch);
+        lg2(cfg.warp_min_buckets), cfg.chunk, quad, cfg.cycle_timing, dag_bnd, pc_scratch,
+        cfg.pop_contiguous ? 0 : 1);
     return cudaGetLastError();
 }
 

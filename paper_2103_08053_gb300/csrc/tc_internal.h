@@ -62,6 +62,7 @@ struct CountCfg {
     int edge_centric;  // 1: Algorithm 2 ablation (table of N+(u) rebuilt for every out-edge)
     int balance;       // TC_BALANCE_*: how warp workers spread 2-hop lists over lanes (Sec. 4.2)
     int warp_order;    // 0 auto, 1 warp list grouped by locality key, 2 vertex order
+    int pop_contiguous = 0;  // 1: warp workers pop consecutive warp-list entries (batches)
 };
 
 // One graph of an orientation pass. A batch places its graphs in one padded
