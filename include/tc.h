@@ -131,8 +131,10 @@ typedef struct {
                                     N(u) -- so that vertices with overlapping neighbourhoods are counted
                                     together and share the 2-hop lists they read in L2 (unsorted rows
                                     give an arbitrary order); 2 vertex order. Same counts in every mode.
-                                    Single-graph calls on a CSR with fewer than 2^31 entries (tc_count,
-                                    tc_count_async, tc_count_host); batches use vertex order. */
+                                    Single-graph calls: tc_count, tc_count_async, tc_count_host on a CSR
+                                    with fewer than 2^31 entries, and tc_count_dag, whose key takes the
+                                    first out-neighbour (the smallest of N+(u) for sorted lists); batches
+                                    use vertex order. */
 } tc_params;
 
 /* tc_params.balance (Sec. 4.2's intra-vertex workload balancing methods) */

@@ -314,6 +314,7 @@ static tc_status order_keys(tc_ctx* ctx, Workspace& ws, int64_t n, int64_t nnz, 
     tc_status s;
     if ((s = ws.okey.ensure(ctx, (size_t)(n + 1) * 4, st))) return s;
     if ((s = ws.ohist.ensure(ctx, (size_t)(n + 1) * 4, st))) return s;
+    if ((s = ws.partial.ensure(ctx, (size_t)(scan_blocks(n) + 2) * 8, st))) return s;
     *ncol = col;
     return TC_OK;
 }
@@ -505,11 +506,15 @@ tc_status tc_count_dag(tc_ctx* ctx, const tc_dag* dag, uint64_t* count_host, uin
     cudaStream_t st = (cudaStream_t)stream;
     tc_status s = ensure_count_ws(ctx, ctx->ws, dag->n, dag->m, st);
     if (s) return s;
+    const int32_t* ncol = nullptr;  // ordered warp list: keys from the DAG's own lists
+    if ((s = order_keys(ctx, ctx->ws, dag->n, 2 * dag->m, dag->dag_col, st, &ncol))) return s;
     s = cuda_status(ctx, cudaMemsetAsync(ctx->ws.ctr.p, 0, sizeof(DevCounters), st), "memset counters");
     TimedCall* tm = timing_begin(ctx, false);
     timing_mark(tm, 0, st);
     timing_mark(tm, 1, st);
-    if (!s) s = enqueue_count(ctx, ctx->ws, dag->dag_ptr, dag->dag_col, dag->n, per_vertex_device, st, tm);
+    if (!s)
+        s = enqueue_count(ctx, ctx->ws, dag->dag_ptr, dag->dag_col, dag->n, per_vertex_device, st, tm, nullptr, -1,
+                          ncol);
     DevCounters c;
     if (!s) s = read_counters(ctx, ctx->ws, st, &c);
     if (s) return s;

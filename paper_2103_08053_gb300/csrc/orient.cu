@@ -579,11 +579,12 @@ __global__ void __launch_bounds__(SCAN_THREADS)
 // ---- binning ----------------------------------------------------------------
 
 // ncol != nullptr (ordered warp list; ncol: the input CSR's neighbour ids,
-// whose rows start where the row-local DAG's do): instead of appending a
-// warp-class vertex to the warp list, give it the locality key min(u, first
-// neighbour of u) -- the smallest id of the closed neighbourhood {u} + N(u)
-// when rows are sorted, a min-hash of N(u) -- in okey[u] and count it in
-// ohist[key]; k_place then lays the list out in key order.
+// whose rows start where the row-local DAG's do, or a compact DAG's own
+// lists): instead of appending a warp-class vertex to the warp list, give it
+// the locality key min(u, first entry of its row) -- with sorted rows the
+// smallest id of {u} + N(u) (row-local) or {u} + N+(u) (compact DAG), a
+// min-hash of the neighbourhood -- in okey[u] and count it in ohist[key];
+// k_place then lays the list out in key order.
 __global__ void k_bin(const int32_t* __restrict__ dag_ptr, const int2* __restrict__ dag_bnd, int64_t n,
                       int warp_max, int item_nbrs, int shard_count, int shard_index, int32_t* __restrict__ warp_list,
                       int2* __restrict__ warp_desc, int2* __restrict__ items, int64_t item_cap, long long max_m,
@@ -646,14 +647,15 @@ __global__ void k_bin(const int32_t* __restrict__ dag_ptr, const int2* __restric
 // vertices with the same key sit next to each other in the list and are
 // counted at about the same time; their out-neighbours overlap, so the 2-hop
 // lists they read are shared in L2. The order within a run is arbitrary.
-__global__ void k_place(const int2* __restrict__ dag_bnd, int64_t n, int warp_max, int shard_count, int shard_index,
+__global__ void k_place(const int32_t* __restrict__ dag_ptr, const int2* __restrict__ dag_bnd, int64_t n,
+                        int warp_max, int shard_count, int shard_index,
                         const int32_t* __restrict__ okey, int32_t* __restrict__ ohist, int32_t* __restrict__ warp_list,
                         int2* __restrict__ warp_desc, DevCounters* ctr) {
     if (ctr->err) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += stride) {
         if (shard_count > 1 && (int)(u % shard_count) != shard_index) continue;
-        const int2 b = dag_bnd[u];
+        const int2 b = dag_bnd ? dag_bnd[u] : make_int2(dag_ptr[u], dag_ptr[u + 1] - dag_ptr[u]);
         if (b.y >= 2 && b.y <= warp_max) {
             const int pos = atomicAdd(&ohist[okey[u]], 1);
             warp_list[pos] = (int32_t)u;
@@ -771,7 +773,7 @@ cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, i
                        long long* launches, const int2* dag_bnd, long long max_m, const int32_t* ncol,
                        int32_t* okey, int32_t* ohist, long long* partial) {
     if (n <= 0) return cudaSuccess;
-    if (!dag_bnd || !ncol) okey = nullptr;
+    if (!ncol) okey = nullptr;
     int g = (int)((n + 255) / 256);
     if (g > num_sms * 16) g = num_sms * 16;
     if (okey) {
@@ -787,8 +789,8 @@ cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, i
     k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(ohist, n, partial);
     k_scan_top<<<1, SCAN_TOP_THREADS, 0, st>>>(partial, nb, ohist, n, ctr, 1);
     k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(ohist, n, partial, ohist);
-    k_place<<<g, 256, 0, st>>>(dag_bnd, n, cfg.warp_max_out_degree, cfg.shard_count, cfg.shard_index, okey, ohist,
-                               warp_list, warp_desc, ctr);
+    k_place<<<g, 256, 0, st>>>(dag_ptr, dag_bnd, n, cfg.warp_max_out_degree, cfg.shard_count, cfg.shard_index, okey,
+                               ohist, warp_list, warp_desc, ctr);
     return cudaGetLastError();
 }
 

@@ -119,11 +119,11 @@ cudaError_t launch_orient_batch(const GraphRef* graphs, int k, int offset_bits, 
                                 int2* bnd = nullptr, int32_t* rdag = nullptr, long long entries = 0);
 
 // Binning (Sec. 4.3) from an existing DAG: fills warp_list / items / counters.
-// ncol (the input CSR's neighbour ids; row-local DAG of one graph only; okey,
-// ohist: n ints, partial: scan_blocks(n) + 2 long longs): the warp list is
-// laid out in the order of a locality key, min(u, first neighbour of u) --
-// a histogram of the keys, its scan, and a placement pass -- instead of in
-// vertex order.
+// ncol (one graph only: the input CSR's neighbour ids for a row-local DAG, the
+// DAG's own dag_col for a compact one; okey, ohist: n ints, partial:
+// scan_blocks(n) + 2 long longs): the warp list is laid out in the order of a
+// locality key, min(u, first entry of u's row) -- a histogram of the keys,
+// its scan, and a placement pass -- instead of in vertex order.
 cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* warp_desc,
                        int2* items, int64_t item_cap, DevCounters* ctr, int num_sms, cudaStream_t st,
                        long long* launches,

@@ -313,6 +313,15 @@ def test_ordered_warp_list_launches_and_host_pieces(T):
         assert c.count(g.n, rp, col) == oracle.count(g)
         assert c.kernel_launches() - l0 == 11
         assert gpu_count(c, G.shuffle_rows(g, 3)) == oracle.count(g)   # unsorted rows: an arbitrary order
+        # a compact DAG (tc_orient) counted with the ordered list, per vertex
+        d = c.orient(g.n, rp, col)
+        pv = torch.zeros(g.n, dtype=torch.int64, device="cuda")
+        l1 = c.kernel_launches()
+        want_total, want_pv = oracle.count_dag(oracle.orient(g), per_vertex=True)
+        assert c.count_dag(d, per_vertex=pv) == want_total
+        assert c.kernel_launches() - l1 == 7      # ordered binning (5) + 2 counting
+        assert np.array_equal(pv.cpu().numpy().astype(np.uint64), want_pv)
+        d.free()
         want = oracle.count(big)
         for bits in (32, 64):
             rph = np.ascontiguousarray(big.row_ptr.astype(np.int64 if bits == 64 else np.int32))
