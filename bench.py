@@ -479,7 +479,7 @@ def run_gb300(args):
     t_e = time.perf_counter()
     for _ in range(e2e_steps):
         t_s = time.perf_counter()
-        ctx.count_host(g.n, rp_pin.numpy(), col_pin.numpy(), stream=stream)
+        e2e_count = ctx.count_host(g.n, rp_pin.numpy(), col_pin.numpy(), stream=stream)
         e2e_each.append((time.perf_counter() - t_s) * 1e3)
     torch.cuda.synchronize(dev)
     e2e_mean_ms = (time.perf_counter() - t_e) * 1e3 / e2e_steps
@@ -539,6 +539,7 @@ def run_gb300(args):
                 "max_ms_per_step": max(e2e_each),
                 "h2d_bytes_per_step": int(rp_h.nbytes + col_h.nbytes), "d2h_bytes_per_step": 16,
                 "h2d_copy_ms": h2d_ms, "host_pinned": bool(col_pin.is_pinned()),
+                "count_equal_device": e2e_count == my_count,
                 "api": "tc_count_host (pinned host CSR)"},
         "gpu_launches": launches,
         "clocks": clocks,
