@@ -547,8 +547,9 @@ __global__ void __launch_bounds__(SCAN_TOP_THREADS)
 }
 
 __global__ void __launch_bounds__(SCAN_THREADS)
-    k_scan_down(const int32_t* __restrict__ in, int64_t n, const long long* __restrict__ partial,
-                int32_t* __restrict__ out) {
+    k_scan_down(const int32_t* in, int64_t n, const long long* __restrict__ partial, int32_t* out) {
+    // in and out may be the same array (the ordered warp list scans in place):
+    // a block reads its whole tile before it writes any of it
     __shared__ int s_tile[SCAN_TILE];
     __shared__ long long sh[33];
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
