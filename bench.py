@@ -587,7 +587,10 @@ def run_reference(args):
         return  # the CPU oracle runs once, on rank 0
     import oracle
     g = make_graph(REF_SAMPLE)
-    cores = oracle.max_threads()
+    # rank 0 alone does the work: all host cores, whatever OMP_NUM_THREADS
+    # the launcher set for its ranks
+    cores = max(oracle.max_threads(), len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity")
+                else (os.cpu_count() or 1))
     for _ in range(args.warmup):
         oracle.count(g, threads=cores)
     times = []
