@@ -544,11 +544,14 @@ def run_gb300(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
-    if args.batched:
+    # the batched, served and study sections and the CPU baseline are
+    # single-GPU measurements: a multi-rank run reports the sharded step only
+    single = world == 1
+    if args.batched and single:
         result["batched"] = measure_batched(T, torch, dev, steps=args.batch_steps)
-    if args.serve_seconds > 0:
+    if args.serve_seconds > 0 and single:
         result["serving"] = measure_serving(T, torch, dev, args.serve_seconds)
-    if args.reorder:
+    if args.reorder and single:
         import numpy as np
 
         import graphgen as G
@@ -557,7 +560,7 @@ def run_gb300(args):
               "rmat-s22-ef16-seed5": (big.n, torch.from_numpy(big.row_ptr.astype(np.int32)).to(dev),
                                       torch.from_numpy(np.ascontiguousarray(big.col, dtype=np.int32)).to(dev))}
         result["reorder_study"] = measure_reorder(T, torch, dev, gs)
-    if args.ablation:
+    if args.ablation and single:
         import numpy as np
 
         import graphgen as G
@@ -566,7 +569,7 @@ def run_gb300(args):
               "rmat-s16-ef16-seed1": (small.n, torch.from_numpy(small.row_ptr.astype(np.int32)).to(dev),
                                       torch.from_numpy(np.ascontiguousarray(small.col, dtype=np.int32)).to(dev))}
         result["ablation_study"] = measure_ablation(T, torch, dev, gs)
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and single:
         import oracle
         cores = oracle.max_threads()
         t = time.perf_counter()
