@@ -114,8 +114,9 @@ typedef struct {
                                     2: also count the workers' cycles in table builds and in probes
                                     (blocking calls: tc_count, tc_count_dag, tc_count_host) */
     int32_t hash_mode;           /* 0: multiplicative hashing (default); 1: x mod B, Algorithm 1's hash */
-    int32_t scalar_loads;        /* 0: warp workers read 2-hop lists as aligned 16-byte quads (default);
-                                    1: one key per lane per load */
+    int32_t scalar_loads;        /* 0: warp workers read 2-hop lists as aligned 16-byte quads, or 32-byte
+                                    octets for runs of long lists when dag_col is 32-byte aligned
+                                    (default); 1: one key per lane per load */
     int32_t edge_centric;        /* 1: ablation of Sec. 3.3's edge-centric design (Algorithm 2): the table
                                     of N+(u) is rebuilt for every out-edge (u, v) and probed with N+(v);
                                     slow by design, same counts (default 0) */

@@ -68,6 +68,13 @@ static_assert(VC_UNROLL == 4, "the bitmap owner path reads four window words at 
 #define PACK_MIN_BLOCKS 4
 #endif
 
+#ifndef PACK_OCTETS
+#define PACK_OCTETS 1  // 1: warp workers read 2-hop lists as 32-byte octets when aligned
+#endif
+#ifndef OCT_MIN_AVG
+#define OCT_MIN_AVG 64  // octets for a chunk whose non-empty 2-hop lists average this many keys
+#endif
+
 #ifndef BLOCK_PIECE
 #define BLOCK_PIECE 512  // combined 2-hop indices per piece of a thread-block item (fixed pieces)
 #endif
@@ -500,6 +507,115 @@ __device__ __forceinline__ uint32_t vc_pack_quad(int s, int l, int td, const int
     return hits;
 }
 
+// 256-bit variant of vc_pack_quad: the 2-hop lists are read as aligned
+// 32-byte octets of dag_col (one 256-bit load per lane gives eight keys),
+// halving the owner search, shuffles and address arithmetic per key once
+// more, at the price of more masked slots at list ends. dag_col must be
+// 32-byte aligned; m = readable entries, an octet reaching past it is read
+// entry by entry. One octet per lane per step.
+struct Octet {
+    int v[8];
+};
+__device__ __forceinline__ Octet ld_octet(const int32_t* p) {
+    Octet r;
+    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r.v[0]), "=r"(r.v[1]), "=r"(r.v[2]), "=r"(r.v[3]), "=r"(r.v[4]), "=r"(r.v[5]), "=r"(r.v[6]),
+          "=r"(r.v[7])
+        : "l"(p));
+    return r;
+}
+template <bool SLOT_HITS, int HM, int SL>
+__device__ __forceinline__ uint32_t vc_pack_oct(int s, int l, int td, const int* sm,
+                                                const int32_t* __restrict__ dag_col, int m, int lane, int* stage,
+                                                unsigned mult) {
+    const unsigned nem = __ballot_sync(FULL, l > 0);
+    if (nem == 0) return 0;
+    const int c = __popc(nem);
+    if (l > 0) {
+        const int p = __popc(nem & lanemask_lt(lane));
+        stage[p] = s;
+        stage[32 + p] = s + l;
+        stage[64 + p] = td;
+    }
+    __syncwarp();
+    const bool lst = lane < c;
+    const int cs = lst ? stage[lane] : 0;
+    const int ce = lst ? stage[32 + lane] : 0;
+    const int ctd = stage[64 + (lst ? lane : 0)];  // lanes past the lists alias list 0's table
+    __syncwarp();
+    const int no = lst ? ((ce + 7) >> 3) - (cs >> 3) : 0;
+    const int P = warp_incl_scan(no, lane);
+    const int total = __shfl_sync(FULL, P, 31);
+    const int Pex = P - no;
+    const int obias = (cs >> 3) - Pex;  // global octet index of combined octet f of this list: obias + f
+    const unsigned le = lanemask_le(lane);
+    uint32_t hits = 0;
+    unsigned* bm = reinterpret_cast<unsigned*>(stage + 160);
+    const bool use_bm = total <= 32 * BITMAP_WORDS;
+    if (use_bm) {
+        bm[lane] = 0u;
+        bm[lane + 32] = 0u;
+        __syncwarp();
+        if (lst) atomicOr(&bm[Pex >> 5], 1u << (Pex & 31));
+        __syncwarp();
+    }
+    int cum = 0;
+    int run_slot = 0, run_hits = 0;  // per-vertex hits per run of one pack slot (as in vc_pack_quad)
+    for (int base = 0; base < total; base += 32) {
+        int o;
+        if (use_bm) {
+            const unsigned w0 = bm[base >> 5];
+            o = (cum + __popc(w0 & le) - 1) & 31;
+            cum += __popc(w0);
+        } else {
+            o = vc_owner(base, P, Pex, lst, le) & 31;
+        }
+        const int ob = __shfl_sync(FULL, obias, o);
+        const int so = __shfl_sync(FULL, cs, o);
+        const int eo = __shfl_sync(FULL, ce, o);
+        const int kd = __shfl_sync(FULL, ctd, o);
+        const int f = base + lane;
+        const int x0 = 8 * (ob + f);  // dag_col index of the octet's first slot
+        Octet k;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) k.v[j] = NOKEY;
+        int lo = 8, hi = 0;
+        if (f < total) {
+            lo = so - x0;
+            hi = eo - x0;
+            if (x0 + 7 < m) {
+                k = ld_octet(dag_col + x0);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 7; ++j)
+                    if (x0 + j < m) k.v[j] = __ldg(dag_col + x0 + j);
+            }
+        }
+        const int lg = (kd >> 16) & 31;
+        const int tab = kd & 0xffff;
+        int hq = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (j >= lo && j < hi) {
+                const int h = bucket_of<HM>(k.v[j], lg, mult);
+                hq += Bucket<SL>::at(sm, tab, h).match(k.v[j]);
+            }
+        }
+        hits += hq;
+        if (SLOT_HITS) {
+            const int sl = (kd >> 21) & 31;
+            if (sl != run_slot) {
+                if (run_hits) atomicAdd(&stage[128 + run_slot], run_hits);
+                run_slot = sl;
+                run_hits = 0;
+            }
+            run_hits += hq;
+        }
+    }
+    if (SLOT_HITS && run_hits) atomicAdd(&stage[128 + run_slot], run_hits);
+    return hits;
+}
+
 // Quad-vectorised variant of vc_range_b4 for one table (thread-block
 // workers): lane i brings the list dag_col[s, e) with nq quads; the combined
 // quad indices [skip, min(limit, total)) are dealt one per lane, QUAD_UNROLL
@@ -738,7 +854,12 @@ __device__ __forceinline__ void list_bounds(int v, const int32_t* __restrict__ d
 // first, then all their length words.
 // BAL: TC_BALANCE_VC (the design) or one of the Sec. 4.2 alternatives above;
 // pc_buf: the physical combination's scratch, PC_ROUND pairs per warp.
-template <bool PER_VERTEX, int HM, int BAL>
+// OCT: the octet-capable build. With quad == 2 both builds are launched, one
+// after the other, and only the one that fits the graph's shape works: the
+// octet build when at least 1 % of the counted vertices are thread-block
+// vertices (a skewed graph, whose warp workers probe long 2-hop lists), the
+// quad build otherwise.
+template <bool PER_VERTEX, int HM, int BAL, bool OCT = false>
 __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
     k_count_pack(const int32_t* __restrict__ dag_ptr, const int32_t* __restrict__ dag_col,
                  const int2* __restrict__ desc, const int32_t* __restrict__ warp_list,
@@ -747,6 +868,7 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
                  int2* __restrict__ pc_buf, int strided) {
     extern __shared__ int smem[];
     if (ctr->err) return;
+    if (quad == 2 && (100LL * ctr->n_block >= (long long)ctr->n_warp) != OCT) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int m = quad ? (dag_bnd ? dag_bnd[n].x : __ldg(dag_ptr + n)) : 0;  // readable dag_col entries
     long long cyc_b = 0, cyc_p = 0;               // build / probe cycles (timing only)
@@ -876,6 +998,13 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
                         hits += balance_pc<PER_VERTEX, HM, PACK_SLOTS>(
                             s, l, td, smem, dag_col, lane, stage, mult,
                             pc_buf + ((size_t)blockIdx.x * (blockDim.x >> 5) + w) * PC_ROUND);
+                } else if (OCT && !chained && quad == 2 &&
+                           __reduce_add_sync(FULL, (unsigned)l) >=
+                               (unsigned)OCT_MIN_AVG * __popc(__ballot_sync(FULL, l > 0))) {
+                    // octets pay off on long 2-hop lists; on short ones their alignment
+                    // and tail slots cost more than the saved owner work (quads below)
+                    hits += vc_pack_oct<PER_VERTEX, HM, PACK_SLOTS>(s, l, etab | (elg << 16) | (eslot << 21), smem,
+                                                                    dag_col, m, lane, stage, mult);
                 } else if (!chained && quad) {
                     hits += vc_pack_quad<PER_VERTEX, HM, PACK_SLOTS>(s, l, etab | (elg << 16) | (eslot << 21), smem, dag_col,
                                                          m, lane, stage, mult);
@@ -1233,6 +1362,13 @@ PackKernel pack_kernel(bool per_vertex, int hm, int bal = TC_BALANCE_VC) {
     return per_vertex ? k_count_pack<true, 0, TC_BALANCE_VC> : k_count_pack<false, 0, TC_BALANCE_VC>;
 }
 
+// the octet-capable build (virtual combination only)
+PackKernel pack_kernel_oct(bool per_vertex, int hm) {
+    if (hm == 1)
+        return per_vertex ? k_count_pack<true, 1, TC_BALANCE_VC, true> : k_count_pack<false, 1, TC_BALANCE_VC, true>;
+    return per_vertex ? k_count_pack<true, 0, TC_BALANCE_VC, true> : k_count_pack<false, 0, TC_BALANCE_VC, true>;
+}
+
 using BlockKernel = void (*)(const int32_t*, const int32_t*, const int2*, unsigned long long*, DevCounters*, int,
                              int, int, int, int, int, const int2*);
 
@@ -1293,9 +1429,13 @@ int count_block_part_max(const CountCfg& cfg) {
 cudaError_t count_kernel_setup(CountCfg& cfg, int num_sms) {
     const int warp_smem = pack_smem_bytes(cfg);
     cudaError_t e = cudaSuccess;
-    for (int pv = 0; pv < 2 && e == cudaSuccess; ++pv)
+    for (int pv = 0; pv < 2 && e == cudaSuccess; ++pv) {
         e = cudaFuncSetAttribute(pack_kernel(pv, cfg.hash_mode, cfg.balance),
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(pack_kernel_oct(pv, cfg.hash_mode), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     warp_smem);
+    }
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(block_kernel(cfg.hash_mode), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              cfg.block_smem_bytes);
@@ -1330,14 +1470,27 @@ cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t
     *launches += 2;
     const int table_off = (cfg.block_threads / 32) * BLOCK_STAGE_INTS + 3 * cfg.item_neighbors;
     const int quad = (cfg.quad_loads && ((uintptr_t)dag_col & 15) == 0) ? 1 : 0;
+    // warp workers: with 32-byte aligned lists (PACK_OCTETS, virtual combination)
+    // both the quad and the octet-capable builds are launched; the graph's
+    // shape, known on the device after binning, picks the one that runs
+    const int pack_quad =
+        (quad && PACK_OCTETS && cfg.balance == TC_BALANCE_VC && ((uintptr_t)dag_col & 31) == 0) ? 2 : quad;
     block_kernel(cfg.hash_mode)<<<cfg.block_grid, cfg.block_threads, cfg.block_smem_bytes, st>>>(
         dag_ptr, dag_col, items, per_vertex, ctr, (int)n, table_off, count_block_part_max(cfg), cfg.item_neighbors,
         quad, cfg.cycle_timing, dag_bnd);
     pack_kernel(per_vertex != nullptr, cfg.hash_mode, cfg.balance)<<<cfg.warp_grid, cfg.warps_per_block * 32,
                                                                    pack_smem_bytes(cfg), st>>>(
         dag_ptr, dag_col, warp_desc, warp_list, per_vertex, ctr, (int)n, cfg.warp_area_ints,
-        lg2(cfg.warp_min_buckets), cfg.chunk, quad, cfg.cycle_timing, dag_bnd, pc_scratch,
+        lg2(cfg.warp_min_buckets), cfg.chunk, pack_quad, cfg.cycle_timing, dag_bnd, pc_scratch,
         cfg.pop_contiguous ? 0 : 1);
+    if (pack_quad == 2) {
+        *launches += 1;
+        pack_kernel_oct(per_vertex != nullptr, cfg.hash_mode)<<<cfg.warp_grid, cfg.warps_per_block * 32,
+                                                                pack_smem_bytes(cfg), st>>>(
+            dag_ptr, dag_col, warp_desc, warp_list, per_vertex, ctr, (int)n, cfg.warp_area_ints,
+            lg2(cfg.warp_min_buckets), cfg.chunk, pack_quad, cfg.cycle_timing, dag_bnd, pc_scratch,
+            cfg.pop_contiguous ? 0 : 1);
+    }
     return cudaGetLastError();
 }
 

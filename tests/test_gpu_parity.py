@@ -195,16 +195,16 @@ def test_balance_modes_per_vertex_and_long_lists(T, balance):
 
 
 def test_unaligned_dag_and_ragged_quads(ctx):
-    # 16-byte quad loads need an aligned dag_col; a DAG whose dag_col starts 4
-    # bytes past an alignment boundary is probed one key per lane. Both must
-    # equal the oracle, including the per-vertex counts, and so must a DAG
-    # whose last list ends at a length that is not a multiple of 4.
+    # wide loads need an aligned dag_col: 32-byte octets at shift 0, 16-byte
+    # quads at shift 4 (16 bytes), one key per lane otherwise. All must equal
+    # the oracle, including the per-vertex counts, and so must a DAG whose last
+    # list ends at a length that is not a multiple of 4.
     g = G.rmat(12, 12, seed=21)
     od = oracle.orient(g)
     want_total, want_pv = oracle.count_dag(od, per_vertex=True)
     dp = torch.from_numpy(od.dag_ptr.astype(np.int32)).cuda()
-    for shift in (0, 1, 2, 3):
-        buf = torch.zeros(od.m + 4, dtype=torch.int32, device="cuda")
+    for shift in (0, 1, 2, 3, 4, 5):
+        buf = torch.zeros(od.m + 8, dtype=torch.int32, device="cuda")
         buf[shift:shift + od.m] = torch.from_numpy(od.dag_col).cuda()
         dc = buf[shift:shift + od.m]
         raw = T_tc().tc_dag(g.n, od.m, dp.data_ptr(), dc.data_ptr())
@@ -311,7 +311,7 @@ def test_ordered_warp_list_launches_and_host_pieces(T):
         rp, col = dev(g)
         l0 = c.kernel_launches()
         assert c.count(g.n, rp, col) == oracle.count(g)
-        assert c.kernel_launches() - l0 == 11
+        assert c.kernel_launches() - l0 == 12
         assert gpu_count(c, G.shuffle_rows(g, 3)) == oracle.count(g)   # unsorted rows: an arbitrary order
         # a compact DAG (tc_orient) counted with the ordered list, per vertex
         d = c.orient(g.n, rp, col)
@@ -319,7 +319,7 @@ def test_ordered_warp_list_launches_and_host_pieces(T):
         l1 = c.kernel_launches()
         want_total, want_pv = oracle.count_dag(oracle.orient(g), per_vertex=True)
         assert c.count_dag(d, per_vertex=pv) == want_total
-        assert c.kernel_launches() - l1 == 7      # ordered binning (5) + 2 counting
+        assert c.kernel_launches() - l1 == 8      # ordered binning (5) + 3 counting
         assert np.array_equal(pv.cpu().numpy().astype(np.uint64), want_pv)
         d.free()
         want = oracle.count(big)
@@ -413,12 +413,13 @@ def test_phase_timing_and_launch_count(T):
         rp, col = dev(g)
         l0 = c.kernel_launches()
         assert c.count(g.n, rp, col) == oracle.count(g)
-        # row-local DAG: degree + 2 orientation count kernels, bin, 2 counting, finish
-        assert c.kernel_launches() - l0 == 7
+        # row-local DAG: degree + 2 orientation count kernels, bin, 3 counting (block
+        # workers, quad and octet builds of the warp workers), finish
+        assert c.kernel_launches() - l0 == 8
         d = c.orient(g.n, rp, col)              # a compact DAG: 8 orientation kernels
         l1 = c.kernel_launches()
         assert c.count_dag(d) == oracle.count(g)
-        assert c.kernel_launches() - l1 == 3     # bin + 2 counting
+        assert c.kernel_launches() - l1 == 4     # bin + 3 counting
         d.free()
         t = c.read_timing()
         assert t["calls"] == 2 and t["orient_ms"] > 0 and t["count_ms"] > 0
