@@ -25,6 +25,7 @@ import re
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -175,8 +176,8 @@ def measure_batched(T, torch, dev, steps: int):
     edges = sum(g.m for g in gs)
     with T.Context(dev.index) as c:
         t = time.time()
-        tuned = c.autotune(tensors, cache_path=os.path.join(ROOT, "gpurun_out", "tune_cache.txt")
-                           if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+        # the tuner's on-disk cache lives in the system's temporary directory
+        tuned = c.autotune(tensors, cache_path=os.path.join(tempfile.gettempdir(), "trust_gb300_tune_cache.txt"))
         tune_s = time.time() - t
         counts = c.count_batch(tensors)  # first call captures the CUDA graph
         c.count_batch(tensors)
