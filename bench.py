@@ -336,7 +336,7 @@ def measure_ablation(T, torch, dev, graphs):
     one-key loads) vs warp-centric, subwarps of 8 and 16 lanes and physical
     combination. count_ms is timed without the cycle counters; the count must
     be the same in every mode."""
-    modes = [("vertex-centric, VC, quad loads (default)", {}),
+    modes = [("vertex-centric, VC, 16- or 32-byte loads (default)", {}),
              ("vertex-centric, VC, scalar loads", dict(scalar_loads=1)),
              ("vertex-centric, warp-centric (WC)", dict(balance=T.TC_BALANCE_WC)),
              ("vertex-centric, subwarp 8 (SW8)", dict(balance=T.TC_BALANCE_SW8)),
