@@ -1,0 +1,46 @@
+"""bench.py's JSON contract on CPU: the reference arm (the oracle timed on the
+host cores) prints one line with the keys the driver reads, and the
+argument parser accepts the documented flags. No GPU is needed."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def run(*args, env=None, timeout=600):
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], cwd=ROOT, env=env,
+                          capture_output=True, text=True, timeout=timeout)
+
+
+def test_reference_arm_prints_one_contract_line():
+    env = dict(os.environ, OMP_NUM_THREADS="1")  # as a launcher sets it: the arm must still use all cores
+    r = run("--impl", "reference", "--steps", "1", "--warmup", "3", env=env)
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["metric"] == "triangle-count TEPS" and d["unit"] == "edges/s"
+    assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 3 and d["higher_is_better"] is True
+    assert d["config"]["workload"] == "rgg-2^22-meandeg64-seed2"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] == (
+        len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count())
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_warmup_below_three_is_refused():
+    r = run("--warmup", "2", timeout=120)
+    assert r.returncode != 0 and "warmup" in (r.stderr + r.stdout)
+
+
+def test_documented_flags_parse():
+    r = run("--help", timeout=120)
+    assert r.returncode == 0
+    for flag in ("--gpus", "--steps", "--warmup", "--impl", "--workload", "--batched", "--serve-seconds",
+                 "--reorder", "--ablation", "--reorder-profile", "--profile-hash-mode", "--no-cpu-baseline"):
+        assert flag in r.stdout, flag
