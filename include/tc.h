@@ -289,8 +289,11 @@ tc_status tc_count_dag_noalloc(const tc_dag* dag, uint64_t* count_device, int32_
 /* ---- batched counting ----------------------------------------------------- */
 
 /* Count k independent graphs in one pass: all graphs are oriented by one
- * launch sequence and counted by one persistent kernel whose work items are
- * (graph, vertex) pairs. gs: k device CSRs (int32 or int64 offsets).
+ * launch sequence into one DAG over a padded common vertex space and counted
+ * by one launch of the persistent counting kernels, whose work items are the
+ * vertices of all graphs; per-vertex counts are summed per graph. The launch
+ * sequence is captured into a CUDA graph and replayed for batches of the same
+ * shape. gs: k device CSRs (int32 or int64 offsets, one width per batch).
  * counts_host: k results. Blocks. */
 tc_status tc_count_batch(tc_ctx* ctx, const tc_csr* gs, int32_t k, uint64_t* counts_host, void* stream);
 
