@@ -194,6 +194,27 @@ def test_balance_modes_per_vertex_and_long_lists(T, balance):
             assert c.count_batch([(g.n, rp, col), (g.n, rp, col)]) == [want_total, want_total]
 
 
+@pytest.mark.parametrize("skewed", [True, False])
+def test_octet_and_quad_builds_per_vertex(T, skewed):
+    # both builds of the warp workers are launched and the graph's shape picks
+    # one: with a small T_w most counted vertices become thread-block vertices
+    # (the octet build works), with the default T_w the RGG graph has none (the
+    # quad build works); per-vertex counts must equal the oracle's either way
+    g = G.disjoint_union([G.rmat(13, 16, seed=44), G.rgg(20_000, 64.0, seed=45), G.complete(90)])
+    want_total, want_pv = oracle.count_dag(oracle.orient(g), per_vertex=True)
+    prm = dict(warp_max_out_degree=8, item_neighbors=32) if skewed else {}
+    with T.Context(0, params=prm) as c:
+        rp, col = dev(g)
+        d = c.orient(g.n, rp, col)
+        st = c.dag_stats(d)
+        assert (100 * st["n_block"] >= st["n_warp"]) == skewed
+        pv = torch.zeros(g.n, dtype=torch.int64, device="cuda")
+        assert c.count_dag(d, per_vertex=pv) == want_total
+        assert np.array_equal(pv.cpu().numpy().astype(np.uint64), want_pv)
+        d.free()
+        assert c.count(g.n, rp, col) == want_total
+
+
 def test_unaligned_dag_and_ragged_quads(ctx):
     # wide loads need an aligned dag_col: 32-byte octets at shift 0, 16-byte
     # quads at shift 4 (16 bytes), one key per lane otherwise. All must equal
