@@ -13,8 +13,10 @@
  *      small vertices go to warp workers, large ones to thread-block workers;
  *   3. for every vertex u a bucketed hash table of N+(u) is built once in
  *      shared memory (Algorithm 1 hashTableConstruction, Sec. 3.1-3.2:
- *      fixed-size buckets, atomic slot counters, level-major layout, overflow
- *      to the next bucket), then probed with N+(v) for every v in N+(u)
+ *      fixed-size buckets, atomic slot counters, overflow to the next bucket;
+ *      each bucket is stored whole, bucket-major, so that one vector load
+ *      fetches it, where the paper interleaves buckets level by level), then
+ *      probed with N+(v) for every v in N+(u)
  *      (Algorithm 1 intersection / linearSearch), with the 2-hop lists of all
  *      v spread evenly over the lanes by virtual combination (Sec. 4.2);
  *   4. hits are summed into one 64-bit count.
@@ -91,9 +93,12 @@ typedef struct {
 } tc_dag;
 
 /* Tunables. Zero in any field means "use the default" (tc_default_params).
- * The paper's constants are noted beside each (Sec. 3.1, 3.2, 4.3). Every
- * table bucket holds 4 keys (the paper's maximum collision count is 128 with
- * 6 levels cached in shared memory); a fuller bucket overflows to the next. */
+ * The paper's constants are noted beside each (Sec. 3.1, 3.2, 4.3). Table
+ * buckets are small and fixed-size (the paper allows up to 128 keys per bucket,
+ * 6 levels of them cached in shared memory): a warp worker's table has buckets
+ * of 2 keys (one 8-byte load per probe), a thread-block worker's table buckets
+ * of 4 keys (one 16-byte load). A key whose bucket is full goes to the next
+ * bucket. */
 typedef struct {
     int32_t warp_max_out_degree; /* d+ above this -> thread-block worker, <= 255 (paper: 100; default 128) */
     int32_t warp_area_ints;      /* shared-memory table area of one warp worker, ints (default 1152);
@@ -266,7 +271,7 @@ tc_status tc_reorder(tc_ctx* ctx, const tc_csr* g, int32_t kind, int32_t* new_id
  *
  * It counts the triangles of an oriented graph exactly like tc_count_dag with
  * the default tc_params (no per-vertex output), using a scratch array that is a
- * static part of the library on every device that loads it (about 5.3 MB, held
+ * static part of the library on every device that loads it (about 5.8 MB, held
  * until the process exits). dag: device arrays, caller-owned, with
  * n <= TC_NOALLOC_MAX_N and m <= TC_NOALLOC_MAX_M; larger graphs are rejected
  * with TC_ERR_UNSUPPORTED before any GPU work. count_device: device uint64,
@@ -357,6 +362,19 @@ tc_status tc_read_timing(tc_ctx* ctx, tc_timing* out);
 
 /* Number of kernels this context has launched so far. */
 tc_status tc_kernel_launches(tc_ctx* ctx, int64_t* out);
+
+/* Allocation-failure injection for testing error handling (the paper has no
+ * counterpart; its failure model is a memory budget, Sec. 3.2). From now on,
+ * the nth device allocation the context attempts fails on the host as if
+ * the device were out of memory: the call that needed it returns TC_ERR_OOM
+ * (for a served request, tc_submit or the request's tc_poll), no CUDA call
+ * is made for it and nothing runs on the GPU. nth == 0 cancels a pending
+ * failure; after the injected failure the counter is off again. Counted
+ * allocations: workspace growth (grow-only buffers of every entry point),
+ * tc_orient's DAG arrays and the serving arena. The failed call leaves the
+ * context usable: a later call allocates again and counts correctly.
+ * TC_ERR_INVALID_ARG: ctx NULL or nth < 0. */
+tc_status tc_inject_oom(tc_ctx* ctx, int64_t nth);
 
 const char* tc_status_string(tc_status s);
 /* Text of the last failure on ctx (empty if none); with ctx == NULL, the last

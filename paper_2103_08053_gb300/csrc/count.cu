@@ -39,20 +39,25 @@
 // Pack table layout. The paper interleaves buckets level-major so that a warp
 // scanning one level reads global memory coalesced. A pack table lives in
 // shared memory, where each lane reads its own bucket, so a bucket is stored
-// whole: 4 slots = 16 bytes, fetched with one vector load and compared
-// without branches. B = max(min_buckets, 2 * nextpow2(d+)) keeps the load
-// factor <= 1/2, so a bucket is rarely full and the overflow chain is rarely
-// walked. The per-bucket lengths are bytes (4 per word; an atomicAdd of
-// 1 << 8*(h%4) on the word claims a slot of bucket h) and live after the
-// slots: a table is 4B + B/4 ints.
+// whole (bucket-major): PACK_SLOTS = 2 slots = 8 bytes, fetched with one
+// vector load and compared without branches. A table for out-degree d+ has
+// 8 * nextpow2(d+) slots (at least 4 * min_buckets), i.e. 4 * nextpow2(d+)
+// two-slot buckets, so the load factor is <= 1/4 per slot. The per-bucket
+// lengths are bytes (4 per word; an atomicAdd of 1 << 8*(h%4) on the word
+// claims a slot of bucket h) and live after the slots. A pack whose keys do
+// not all fit their home buckets is rebuilt with another hash multiplier, so
+// its probes need no overflow chain (k_count_pack).
 //
-// Thread-block tables use the same bucket-of-4 layout with B = nextpow2(part)
-// buckets (load factor <= 1) and one 32-bit length word per bucket (a bucket
-// of a large table can see more than 255 claims), where N+(u) is split into
-// parts of at most
-// P_max keys (the largest power of two whose table fits the block's shared
-// memory), each probed by the whole 2-hop list:
-// |N+(u) ∩ N+(v)| = sum over parts of |part ∩ N+(v)|.
+// Thread-block tables use 4-slot (16-byte) buckets, B = nextpow2(part)
+// buckets (at most one key per bucket on average) and one 32-bit length word
+// per bucket (a bucket of a large table can see more than 255 claims), where
+// N+(u) is split into parts of at most P_max keys (the largest power of two
+// whose table fits the block's shared memory), each probed by the whole
+// 2-hop list: |N+(u) ∩ N+(v)| = sum over parts of |part ∩ N+(v)|. After a
+// build, buckets that received more claims than slots are marked
+// (mark_overflow); only a marked bucket sends a search on to the next one.
+#include <mutex>
+
 #include "tc_internal.h"
 
 namespace tcg {
@@ -84,11 +89,24 @@ static_assert(VC_UNROLL == 4, "the bitmap owner path reads four window words at 
 #ifndef BLOCK_SLOTS
 #define BLOCK_SLOTS 4  // slots per bucket of the thread-block tables (2: overflow chains at load 1/2 cost more)
 #endif
+#ifndef BLOCK_OVF
+#define BLOCK_OVF 1  // 1: thread-block tables mark overflowed buckets; only those send a search on
+#endif
+#ifndef BLOCK_REHASH
+#define BLOCK_REHASH 1  // 1: a thread-block table with a displaced key is rebuilt with the next hash multiplier (up to 4)
+#endif
+#ifndef BLOCK_SPARSE
+#define BLOCK_SPARSE 0  // log2 of the extra bucket factor of thread-block tables (B = nextpow2(part) << this)
+#endif
 
 constexpr int STAGE_INTS = 224;        // warp workers: 4 x 32 compaction lanes | 32 slot hits | 64-word bitmap
 constexpr int BLOCK_STAGE_INTS = 128;  // thread-block workers: 4 x 32 compaction lanes
 constexpr int EMPTY = -1;        // an unused slot (vertex ids are >= 0)
 constexpr int NOKEY = -2;        // the key of a lane with nothing to probe
+// Bit 31 of a bucket's last slot marks an overflowed bucket of a thread-block
+// table (mark_overflow). A marked slot holds key | OVF_BIT <= -2 for a vertex
+// id key <= 2^31 - 2, so it never equals EMPTY or a key.
+constexpr int OVF_BIT = (int)0x80000000u;
 
 __device__ __forceinline__ unsigned lanemask_le(int lane) { return (2u << lane) - 1u; }
 __device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
@@ -141,11 +159,11 @@ __device__ __forceinline__ int bucket_of(int w, int lgB, unsigned mult = kHashMu
     return (int)(((unsigned)w * mult) >> (32 - lgB));
 }
 
-// ---- pack tables (bucket-major, 4 slots, byte lengths) ---------------------
+// ---- table builds (bucket-major buckets of SL slots) ------------------------
 
 // Algorithm 1 hashTableConstruction, one key: claim a slot of bucket h with
-// an atomic add on its length byte; a full bucket (4 claims) sends the key to
-// the next bucket. sm: shared array; tab/lenw: int offsets of the slots and
+// an atomic add on its length byte; a full bucket (SL claims) sends the key
+// to the next bucket. sm: shared array; tab/lenw: int offsets of the slots and
 // of the length words; B = 2^lgB. Lengths count claims (<= keys <= 255).
 // Returns 1 when the key did not fit its home bucket (the table overflowed).
 template <int HM, int SL = 4>
@@ -169,10 +187,11 @@ __device__ __forceinline__ int insert_b4(int* sm, int tab, int lenw, int lgB, in
 // whose buckets can see more than 255 claims).
 // With SL = 2 the lengths are 16-bit, two per word (a part holds at most
 // 2^16 - 1 keys, so a length never carries into its neighbour).
+// Returns 1 when the key did not fit its home bucket.
 template <int HM, int SL = 4>
-__device__ __forceinline__ void insert_b4w(int* sm, int tab, int lenw, int lgB, int w) {
+__device__ __forceinline__ int insert_b4w(int* sm, int tab, int lenw, int lgB, int w, unsigned mult) {
     const int mask = (1 << lgB) - 1;
-    int h = bucket_of<HM>(w, lgB);
+    int h = bucket_of<HM>(w, lgB, mult);
     for (int s = 0; s <= mask; ++s) {
         int slot;
         if (SL == 4) {
@@ -183,10 +202,11 @@ __device__ __forceinline__ void insert_b4w(int* sm, int tab, int lenw, int lgB, 
         }
         if (slot < SL) {
             sm[tab + SL * h + slot] = w;
-            return;
+            return s > 0;
         }
         h = (h + 1) & mask;
     }
+    return 1;
 }
 
 __device__ __forceinline__ int match4(const int4 q, int w) { return (q.x == w) | (q.y == w) | (q.z == w) | (q.w == w); }
@@ -206,6 +226,11 @@ struct Bucket<4> {
     }
     __device__ __forceinline__ int match(int w) const { return match4(q, w); }
     __device__ __forceinline__ bool full() const { return q.w != EMPTY; }
+    // overflow-marked tables (see mark_overflow): the last slot may carry OVF_BIT
+    __device__ __forceinline__ int match_ovf(int w) const {
+        return (q.x == w) | (q.y == w) | (q.z == w) | ((q.w & ~OVF_BIT) == w);
+    }
+    __device__ __forceinline__ bool overflowed() const { return q.w < EMPTY; }
 };
 template <>
 struct Bucket<2> {
@@ -215,26 +240,58 @@ struct Bucket<2> {
     }
     __device__ __forceinline__ int match(int w) const { return (q.x == w) | (q.y == w); }
     __device__ __forceinline__ bool full() const { return q.y != EMPTY; }
+    __device__ __forceinline__ int match_ovf(int w) const { return (q.x == w) | ((q.y & ~OVF_BIT) == w); }
+    __device__ __forceinline__ bool overflowed() const { return q.y < EMPTY; }
 };
 
-// Algorithm 1 linearSearch continued past a full bucket h0 (slow path).
-template <int SL>
+// Whether a search for a key absent from bucket b must go on to the next
+// bucket. Plain tables (OVF = false): b is full (some key of this home may
+// have been sent on). Overflow-marked tables (OVF = true): b received more
+// claims than it has slots, which mark_overflow records in b's last slot --
+// a bucket that is merely full sends nothing on, so its misses stop there.
+template <int SL, bool OVF>
+__device__ __forceinline__ int bucket_match(const Bucket<SL>& b, int w) {
+    return OVF ? b.match_ovf(w) : b.match(w);
+}
+template <int SL, bool OVF>
+__device__ __forceinline__ bool bucket_more(const Bucket<SL>& b) {
+    return OVF ? b.overflowed() : b.full();
+}
+
+// Algorithm 1 linearSearch continued past bucket h0 (slow path): the
+// successor buckets in order, while bucket_more says a key may lie further on.
+template <int SL, bool OVF = false>
 __device__ __noinline__ int probe_chain(const int* sm, int tab, int mask, int h0, int w) {
     int h = (h0 + 1) & mask;
     for (int s = 0; s < mask; ++s) {
         const Bucket<SL> b = Bucket<SL>::at(sm, tab, h);
-        const int hit = b.match(w);
-        if (hit | !b.full()) return hit;
+        const int hit = bucket_match<SL, OVF>(b, w);
+        if (hit | !bucket_more<SL, OVF>(b)) return hit;
         h = (h + 1) & mask;
     }
     return 0;
 }
 
+// After a thread-block table is built: mark every bucket that received more
+// claims than its SL slots -- a key that hashed there was sent to a later
+// bucket -- by setting OVF_BIT in its last slot (which holds a key, the
+// bucket being full). Claims are the bucket's length counter (32-bit words
+// for SL = 4, 16-bit halves for SL = 2). Called by all threads of the block
+// between two barriers.
+template <int SL>
+__device__ __forceinline__ void mark_overflow(int* sm, int tab, int lenw, int nbuckets) {
+    for (int t = threadIdx.x; t < nbuckets; t += blockDim.x) {
+        const int claims = SL == 4 ? sm[lenw + t] : (int)(((unsigned)sm[lenw + (t >> 1)] >> (16 * (t & 1))) & 0xffffu);
+        if (claims > SL) sm[tab + SL * t + SL - 1] |= OVF_BIT;
+    }
+}
+
 // VC_UNROLL probes per lane: key[q] against the table at int offset kt[q]
 // with log2 B = km[q] & 0xffff (pack slot km[q] >> 16). A probe is one
-// 16-byte load and four compares; only a lane whose bucket is full and did
-// not match walks the overflow chain. NOKEY lanes never match.
-template <bool SLOT_HITS, int HM, int SL>
+// vector load of the bucket (SL slots) and SL compares; only a lane whose
+// bucket may send the key on (bucket_more) and did not match walks the
+// overflow chain. NOKEY lanes never match.
+template <bool SLOT_HITS, int HM, int SL, bool OVF>
 __device__ __forceinline__ uint32_t probe4(const int (&key)[VC_UNROLL], const int (&kt)[VC_UNROLL],
                                            const int (&km)[VC_UNROLL], const int* sm, int* stage, unsigned mult) {
     uint32_t hits = 0;
@@ -243,10 +300,10 @@ __device__ __forceinline__ uint32_t probe4(const int (&key)[VC_UNROLL], const in
         const int lg = km[q] & 0xffff;
         const int h = bucket_of<HM>(key[q], lg, mult);
         const Bucket<SL> b = Bucket<SL>::at(sm, kt[q], h);
-        int hit = b.match(key[q]);
-        const bool more = key[q] >= 0 && !hit && b.full();
+        int hit = bucket_match<SL, OVF>(b, key[q]);
+        const bool more = key[q] >= 0 && !hit && bucket_more<SL, OVF>(b);
         if (__any_sync(FULL, more)) {
-            if (more) hit = probe_chain<SL>(sm, kt[q], (1 << lg) - 1, h, key[q]);
+            if (more) hit = probe_chain<SL, OVF>(sm, kt[q], (1 << lg) - 1, h, key[q]);
         }
         hits += hit;
         if (SLOT_HITS && hit) atomicAdd(&stage[128 + (km[q] >> 16)], 1);
@@ -254,16 +311,16 @@ __device__ __forceinline__ uint32_t probe4(const int (&key)[VC_UNROLL], const in
     return hits;
 }
 
-// Probe the 2-hop lists of up to 32 out-edges against bucket-of-4 tables.
+// Probe the 2-hop lists of up to 32 out-edges against bucketed tables.
 // Lane i brings the list N+(v_i) = dag_col[s, s+l) and the table of its edge
 // (tab: int offset of the slots, lgB = log2 B, slot: pack slot). Empty lists
 // are compacted away (stage: STAGE_INTS ints of smem), the rest are combined
 // virtually, and the combined indices [skip, min(limit, total)) are dealt out
 // 32 at a time, VC_UNROLL windows per step with all loads of a step issued
-// before its probes. A probe is one 16-byte load and four compares; only a
+// before its probes. A probe is one bucket load and SL compares; only a
 // lane whose bucket is full and did not match walks the overflow chain.
 // Returns the hits; *done = number of combined indices processed.
-template <bool SLOT_HITS, int HM, int SL = 4>
+template <bool SLOT_HITS, int HM, int SL = 4, bool OVF = false>
 __device__ __forceinline__ uint32_t vc_range_b4(int s, int l, int tab, int lgB, int slot, int skip, int limit,
                                                 const int* sm, const int32_t* __restrict__ dag_col, int lane,
                                                 int* stage, int* done, unsigned mult = kHashMult0) {
@@ -306,14 +363,14 @@ __device__ __forceinline__ uint32_t vc_range_b4(int s, int l, int tab, int lgB, 
             const int f = b + lane;
             key[q] = (f < end) ? __ldg(dag_col + bo + f) : NOKEY;
         }
-        hits += probe4<SLOT_HITS, HM, SL>(key, kt, km, sm, stage, mult);
+        hits += probe4<SLOT_HITS, HM, SL, OVF>(key, kt, km, sm, stage, mult);
     }
     *done = end > skip ? end - skip : 0;
     return hits;
 }
 
 // Fast probe of whole 2-hop lists against overflow-free pack tables: every
-// key is in its home bucket, so one 16-byte load and four compares decide it.
+// key is in its home bucket, so one bucket load and SL compares decide it.
 // Lane i brings N+(v_i) = dag_col[s, s+l) and its table descriptor
 // td = slots offset | log2 B << 16 | pack slot << 21. Owners of flat indices
 // come from a bitmap of list starts (bit f set iff a list starts at combined
@@ -621,10 +678,10 @@ __device__ __forceinline__ uint32_t vc_pack_oct(int s, int l, int td, const int*
 // quad indices [skip, min(limit, total)) are dealt one per lane, QUAD_UNROLL
 // per step; slots outside their list are masked; a key whose bucket is full
 // and did not match walks the overflow chain. *done = quads processed.
-template <int HM, int SL>
+template <int HM, int SL, bool OVF, bool CHAIN>
 __device__ __forceinline__ uint32_t vc_range_quad(int s, int e, int nq, int tab, int lgB, int skip, int limit,
                                                   const int* sm, const int32_t* __restrict__ dag_col, int m, int lane,
-                                                  int* stage, int* done) {
+                                                  int* stage, int* done, unsigned mult) {
     const unsigned nem = __ballot_sync(FULL, nq > 0);
     if (nem == 0) {
         *done = 0;
@@ -683,20 +740,21 @@ __device__ __forceinline__ uint32_t vc_range_quad(int s, int e, int nq, int tab,
 #pragma unroll
         for (int q = 0; q < QUAD_UNROLL; ++q) {
             const int key[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
-            int more = 0;  // bit j: slot j's bucket was full and did not match
+            int more = 0;  // bit j: slot j's bucket may have sent its key on and did not match
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (j >= lo[q] && j < hi[q]) {
-                    const int h = bucket_of<HM>(key[j], lgB);
+                    const int h = bucket_of<HM>(key[j], lgB, mult);
                     const Bucket<SL> b = Bucket<SL>::at(sm, tab, h);
-                    const int hit = b.match(key[j]);
+                    const int hit = bucket_match<SL, OVF>(b, key[j]);
                     hits += hit;
-                    more |= (!hit && b.full()) << j;
+                    if (CHAIN) more |= (!hit && bucket_more<SL, OVF>(b)) << j;
                 }
             }
-            if (__any_sync(FULL, more)) {
+            if (CHAIN && __any_sync(FULL, more)) {
                 for (int j = 0; j < 4; ++j)
-                    if ((more >> j) & 1) hits += probe_chain<SL>(sm, tab, mask, bucket_of<HM>(key[j], lgB), key[j]);
+                    if ((more >> j) & 1)
+                        hits += probe_chain<SL, OVF>(sm, tab, mask, bucket_of<HM>(key[j], lgB, mult), key[j]);
             }
         }
     }
@@ -1105,19 +1163,37 @@ __global__ void __launch_bounds__(1024, 1)
             // 4 * nextpow2(part) slots in buckets of BLOCK_SLOTS, then one
             // length word per 4 slots (32-bit lengths for 4-slot buckets,
             // two 16-bit lengths for 2-slot buckets)
-            const int B = next_pow2(pk < 32 ? 32 : pk);
+            const int B = next_pow2(pk < 32 ? 32 : pk) << BLOCK_SPARSE;
             const int lgB = 31 - __clz(B) + (BLOCK_SLOTS == 2 ? 1 : 0);  // log2 of the bucket count
             const long long t_build = timing ? clock64() : 0;
             int* tab = smem + table_off;
             const int lenw = table_off + 4 * B;
-            for (int t = threadIdx.x * 4; t < 4 * B; t += blockDim.x * 4)
-                *reinterpret_cast<int4*>(tab + t) = make_int4(EMPTY, EMPTY, EMPTY, EMPTY);
-            for (int t = threadIdx.x; t < B; t += blockDim.x) smem[lenw + t] = 0;
-            if (threadIdx.x == 0) s_piece = 0;
-            __syncthreads();
-            for (int t = threadIdx.x; t < pk; t += blockDim.x)
-                insert_b4w<HM, BLOCK_SLOTS>(smem, table_off, lenw, lgB, __ldg(dag_col + a + p0 + t));
-            __syncthreads();
+            // build; if a key missed its home bucket, rebuild with the next hash
+            // multiplier (BLOCK_REHASH, up to 4 tries) so that every key sits in its
+            // home bucket and probes need no overflow chain; a table that still
+            // overflows is probed with chains (its overflowed buckets marked)
+            unsigned mult = kHashMult0;
+            bool chained = false;
+            for (int attempt = 0;; ++attempt) {
+                for (int t = threadIdx.x * 4; t < 4 * B; t += blockDim.x * 4)
+                    *reinterpret_cast<int4*>(tab + t) = make_int4(EMPTY, EMPTY, EMPTY, EMPTY);
+                for (int t = threadIdx.x; t < B; t += blockDim.x) smem[lenw + t] = 0;
+                if (threadIdx.x == 0) s_piece = 0;
+                __syncthreads();
+                int ovf = 0;
+                for (int t = threadIdx.x; t < pk; t += blockDim.x)
+                    ovf |= insert_b4w<HM, BLOCK_SLOTS>(smem, table_off, lenw, lgB, __ldg(dag_col + a + p0 + t), mult);
+                if (!__syncthreads_or(ovf)) break;
+                if (!BLOCK_REHASH || HM == 1 || attempt == 3) {
+                    chained = true;
+                    if (BLOCK_OVF) {
+                        mark_overflow<BLOCK_SLOTS>(smem, table_off, lenw, 1 << lgB);
+                        __syncthreads();
+                    }
+                    break;
+                }
+                mult = hash_mult(attempt + 1);
+            }
             const long long t_probe = timing ? clock64() : 0;
             if (timing) cyc_b += t_probe - t_build;
             // combined units (quads or keys) per piece: about 2 pieces per warp
@@ -1143,13 +1219,20 @@ __global__ void __launch_bounds__(1024, 1)
                     const int sj = j < cnt ? S[j] : 0;
                     const int base_flat = j0 ? LP[j0 - 1] : 0;
                     int done = 0;
-                    if (quad) {
+                    if (quad && !chained) {
                         const int ej = j < cnt ? E[j] : 0;
-                        h += vc_range_quad<HM, BLOCK_SLOTS>(sj, ej, uj, table_off, lgB, F - base_flat,
-                                                            F1 - base_flat, smem, dag_col, m, lane, stage, &done);
+                        h += vc_range_quad<HM, BLOCK_SLOTS, false, false>(sj, ej, uj, table_off, lgB, F - base_flat,
+                                                                          F1 - base_flat, smem, dag_col, m, lane,
+                                                                          stage, &done, mult);
+                    } else if (quad) {
+                        const int ej = j < cnt ? E[j] : 0;
+                        h += vc_range_quad<HM, BLOCK_SLOTS, BLOCK_OVF, true>(sj, ej, uj, table_off, lgB,
+                                                                             F - base_flat, F1 - base_flat, smem,
+                                                                             dag_col, m, lane, stage, &done, mult);
                     } else {
-                        h += vc_range_b4<false, HM, BLOCK_SLOTS>(sj, uj, table_off, lgB, 0, F - base_flat,
-                                                                 F1 - base_flat, smem, dag_col, lane, stage, &done);
+                        h += vc_range_b4<false, HM, BLOCK_SLOTS, BLOCK_OVF>(sj, uj, table_off, lgB, 0, F - base_flat,
+                                                                            F1 - base_flat, smem, dag_col, lane,
+                                                                            stage, &done, mult);
                     }
                     F += done;
                 }
@@ -1174,8 +1257,8 @@ __global__ void __launch_bounds__(1024, 1)
 // a vertex u and, for every out-edge (u, v), builds the table of N+(u) afresh
 // and probes it with N+(v) -- the table is rebuilt d+(u) times instead of
 // once. Out-lists longer than the warp's area holds are built part by part,
-// each part probed with all of N+(v). Tables are the pack tables' bucket-of-4
-// layout with overflow chains; keys are read one per lane.
+// each part probed with all of N+(v). Tables have 4-slot buckets with byte
+// lengths (insert_b4's layout) and overflow chains; keys are read one per lane.
 template <int HM>
 __global__ void __launch_bounds__(256) k_count_edge(const int32_t* __restrict__ dag_ptr,
                                                    const int32_t* __restrict__ dag_col,
@@ -1417,30 +1500,43 @@ int count_block_budget_ints(const CountCfg& cfg) {
     return cfg.block_smem_bytes / 4 - (cfg.block_threads / 32) * BLOCK_STAGE_INTS - 3 * cfg.item_neighbors;
 }
 
-// Largest part of N+(u) whose bucket-of-4 table (B = nextpow2(part) buckets,
+// Largest part of N+(u) whose thread-block table (B = nextpow2(part) << BLOCK_SPARSE,
 // 4B slots + B length words) fits the budget.
 int count_block_part_max(const CountCfg& cfg) {
     const int budget = count_block_budget_ints(cfg);
     int p = 32;
-    while (5 * (2 * p) <= budget) p *= 2;
+    while ((5 * (2 * p) << BLOCK_SPARSE) <= budget) p *= 2;
     return p;
 }
+
+namespace {
+
+// Raise kernel fn's dynamic shared-memory limit on the current device to at
+// least `bytes`; a higher limit set before (by another context) is kept.
+std::mutex g_smem_limit_mu;
+cudaError_t raise_smem_limit(const void* fn, int bytes) {
+    std::lock_guard<std::mutex> lk(g_smem_limit_mu);
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, fn);
+    if (e != cudaSuccess) return e;
+    if (a.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+}  // namespace
 
 cudaError_t count_kernel_setup(CountCfg& cfg, int num_sms) {
     const int warp_smem = pack_smem_bytes(cfg);
     cudaError_t e = cudaSuccess;
     for (int pv = 0; pv < 2 && e == cudaSuccess; ++pv) {
-        e = cudaFuncSetAttribute(pack_kernel(pv, cfg.hash_mode, cfg.balance),
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem);
+        e = raise_smem_limit(reinterpret_cast<const void*>(pack_kernel(pv, cfg.hash_mode, cfg.balance)), warp_smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(pack_kernel_oct(pv, cfg.hash_mode), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     warp_smem);
+            e = raise_smem_limit(reinterpret_cast<const void*>(pack_kernel_oct(pv, cfg.hash_mode)), warp_smem);
     }
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(block_kernel(cfg.hash_mode), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             cfg.block_smem_bytes);
+    e = raise_smem_limit(reinterpret_cast<const void*>(block_kernel(cfg.hash_mode)), cfg.block_smem_bytes);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(edge_kernel(cfg.hash_mode), cudaFuncAttributeMaxDynamicSharedMemorySize, warp_smem);
+    e = raise_smem_limit(reinterpret_cast<const void*>(edge_kernel(cfg.hash_mode)), warp_smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pack_kernel(false, cfg.hash_mode, cfg.balance),

@@ -140,8 +140,13 @@ cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t
 size_t pc_scratch_bytes(const CountCfg& cfg);
 int count_block_budget_ints(const CountCfg& cfg);
 int count_block_part_max(const CountCfg& cfg);
-// ints of one warp-worker table for out-degree d (2*nextpow2(d) buckets of 4 slots + byte lengths)
+// ints of one warp-worker table for out-degree d (8*nextpow2(d) slots in PACK_SLOTS-slot buckets + byte lengths)
 int pack_table_ints(int max_out_degree, int min_buckets);
+// Resolves cfg's persistent grid sizes and makes sure the counting kernels
+// may be launched with cfg's dynamic shared memory. The kernels' limits are
+// process-wide per device and shared by every context (and by the
+// allocation-free entry point): they are only ever raised, never lowered, so
+// a context with smaller tables cannot break one with larger tables.
 cudaError_t count_kernel_setup(CountCfg& cfg, int num_sms);
 cudaError_t launch_finish(const DevCounters* ctr, unsigned long long* count_out, int* err_out, cudaStream_t st,
                           long long* launches);
@@ -157,9 +162,13 @@ struct DevStats {
 cudaError_t launch_stats(const int32_t* dag_ptr, const int32_t* dag_col, int64_t n, int warp_max_out_degree,
                          DevStats* out, cudaStream_t st);
 
+// Default tc_params.item_neighbors (out-neighbours of a large vertex per
+// thread-block work item).
+constexpr int DEFAULT_ITEM_NEIGHBORS = 256;
+
 // Upper bound on work items produced by binning (one per large vertex plus
 // one per item_neighbors of its out-list).
-inline int64_t item_capacity(int64_t n, int64_t m, int item_neighbors) {
+constexpr int64_t item_capacity(int64_t n, int64_t m, int item_neighbors) {
     return n + m / (item_neighbors > 0 ? item_neighbors : 1) + 1;
 }
 
