@@ -159,6 +159,15 @@ def count(g, threads: int = 0) -> int:
     return int(t)
 
 
+def count_many(graphs, workers: int = 0) -> list:
+    """T(G) of every graph: one oracle.count per graph, single-threaded each,
+    `workers` graphs at a time on host threads (default: all cores)."""
+    import concurrent.futures as cf
+    workers = workers or os.cpu_count() or 1
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+        return list(ex.map(lambda g: count(g, threads=1), graphs))
+
+
 REORDER_INDEGREE = 1
 REORDER_COLLECTIVE = 2
 

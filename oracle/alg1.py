@@ -15,7 +15,9 @@ two cost models of Sec. 4.1 (Eq. 1 and Eq. 2).
 
 Readings taken where the paper leaves a choice (each also listed in the design
 notes):
-* the hash is ``x % B`` (Algorithm 1, ``hash``);
+* the hash is ``x % B`` (Algorithm 1, ``hash``); a table can be given another
+  bucket function instead, which the tests use to pin the multiplicative-hash
+  collision statistics;
 * a full bucket (``len == L``) sends the element to bucket ``(i + 1) % B``,
   and a search continues through successor buckets while the bucket it just
   scanned is full;
@@ -34,15 +36,18 @@ class BucketTable:
     j of bucket i sits at flat position ``j * B + i``.
     """
 
-    def __init__(self, B: int, L: int):
+    def __init__(self, B: int, L: int, hash_fn=None):
         if B < 1 or L < 1:
             raise ValueError("B and L must be positive")
         self.B = B
         self.L = L
+        self.hash_fn = hash_fn          # None: Algorithm 1's x % B; else a callable (x, B) -> bucket
         self.length = [0] * B           # hashTable(i).len = 0 for every i
         self.level = [[None] * B for _ in range(L)]
 
     def hash(self, x: int) -> int:
+        if self.hash_fn is not None:
+            return self.hash_fn(x, self.B)
         return x % self.B
 
     def insert(self, v: int) -> int:
@@ -79,8 +84,8 @@ class BucketTable:
         return max(self.length) if self.length else 0
 
 
-def hash_table_construction(neighbor_list, B: int, L: int) -> BucketTable:
-    t = BucketTable(B, L)
+def hash_table_construction(neighbor_list, B: int, L: int, hash_fn=None) -> BucketTable:
+    t = BucketTable(B, L, hash_fn)
     for v in neighbor_list:
         t.insert(int(v))
     return t
@@ -141,13 +146,14 @@ def cost_eq1(dag_ptr, dag_col, B: int, L: int) -> int:
     return c
 
 
-def phi_eq2(dag_ptr, dag_col, B: int, L: int) -> int:
-    """Eq. 2: sum_u collective_degree(u) * max collision of HT_u."""
+def phi_eq2(dag_ptr, dag_col, B: int, L: int, hash_fn=None) -> int:
+    """Eq. 2: sum_u collective_degree(u) * max collision of HT_u (tables built
+    with Algorithm 1's hash, or with hash_fn)."""
     phi = 0
     for u in range(len(dag_ptr) - 1):
         nu = dag_col[dag_ptr[u]:dag_ptr[u + 1]]
         if not len(nu):
             continue
-        t = hash_table_construction(nu, B, L)
+        t = hash_table_construction(nu, B, L, hash_fn)
         phi += collective_degree(dag_ptr, dag_col, u) * t.max_collision()
     return phi

@@ -221,6 +221,10 @@ class Context:
         self._check(_tc.tc_kernel_launches(self.handle, ctypes.byref(v)))
         return int(v.value)
 
+    def inject_oom(self, nth: int):
+        """tc_inject_oom: the nth device allocation from now fails (host-side)."""
+        self._check(_tc.tc_inject_oom(self.handle, int(nth)))
+
     # batch
     def count_batch(self, graphs, stream=None) -> list:
         """graphs: sequence of (n, row_ptr, col) device arrays."""

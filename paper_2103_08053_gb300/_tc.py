@@ -105,6 +105,7 @@ _protos = {
     "tc_count_dag_noalloc": (c_int32, [_P(tc_dag), c_void_p, c_void_p, c_void_p]),
     "tc_reorder": (c_int32, [c_void_p, _P(tc_csr), c_int32, c_void_p, _P(tc_csr), c_void_p]),
     "tc_kernel_launches": (c_int32, [c_void_p, _P(c_int64)]),
+    "tc_inject_oom": (c_int32, [c_void_p, c_int64]),
     "tc_status_string": (ctypes.c_char_p, [c_int32]),
     "tc_last_error": (ctypes.c_char_p, [c_void_p]),
     "tc_version": (ctypes.c_char_p, []),

@@ -45,8 +45,18 @@ const char* tcg::err_bits_text(int bits) {
     return "";
 }
 
+bool tcg::injected_oom(tc_ctx* ctx) {
+    if (!ctx) return false;
+    long long k = ctx->fail_alloc_in.load();
+    while (k > 0 && !ctx->fail_alloc_in.compare_exchange_weak(k, k - 1)) {
+    }
+    return k == 1;
+}
+
 tc_status tcg::DevBuf::ensure(tc_ctx* ctx, size_t need, cudaStream_t st) {
     if (need <= bytes) return TC_OK;
+    if (injected_oom(ctx))
+        return ctx_fail(ctx, TC_ERR_OOM, "cudaMalloc(workspace): out of memory (injected by tc_inject_oom)");
     if (p) {
         cudaStreamSynchronize(st);
         cudaFree(p);
@@ -95,7 +105,7 @@ static void fill_defaults(tc_params* p) {
     p->warp_min_buckets = 16;
     p->block_threads = 256;
     p->block_smem_bytes = 50 * 1024;
-    p->item_neighbors = 256;
+    p->item_neighbors = DEFAULT_ITEM_NEIGHBORS;
     p->chunk = 32;
     p->warps_per_block = 8;
     p->shard_count = 1;
@@ -459,6 +469,7 @@ tc_status tc_orient(tc_ctx* ctx, const tc_csr* g, tc_dag* out, void* stream) {
     const int64_t cap = g->nnz / 2 + 1;
     int32_t* dp = nullptr;
     int32_t* dc = nullptr;
+    if (injected_oom(ctx)) return ctx_fail(ctx, TC_ERR_OOM, "cudaMalloc(dag): out of memory (injected by tc_inject_oom)");
     cudaError_t e = cudaMalloc(&dp, (size_t)(g->n + 1) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&dc, (size_t)cap * 4);
     if (e != cudaSuccess) {
@@ -778,6 +789,12 @@ tc_status tc_read_timing(tc_ctx* ctx, tc_timing* out) {
 tc_status tc_kernel_launches(tc_ctx* ctx, int64_t* out) {
     if (!ctx || !out) return TC_ERR_INVALID_ARG;
     *out = ctx->launches.load();
+    return TC_OK;
+}
+
+tc_status tc_inject_oom(tc_ctx* ctx, int64_t nth) {
+    if (!ctx || nth < 0) return TC_ERR_INVALID_ARG;
+    ctx->fail_alloc_in.store((long long)nth);
     return TC_OK;
 }
 

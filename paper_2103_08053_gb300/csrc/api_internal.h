@@ -119,11 +119,17 @@ struct tc_ctx {
     cudaEvent_t aux_ev[9] = {};             // one per piece, plus the start
     tcg::BatchRunner* batch = nullptr;
     tcg::ServeState* serve = nullptr;
+    // tc_inject_oom: the fail_alloc_in-th counted device allocation from now
+    // on fails on the host as if the device were out of memory (0: off)
+    std::atomic<long long> fail_alloc_in{0};
 };
 
 namespace tcg {
 
 tc_status ctx_fail(tc_ctx* ctx, tc_status s, const char* fmt, ...);
+// True when this device allocation of ctx is the one tc_inject_oom asked to
+// fail (it then counts as made); false otherwise, and always for ctx NULL.
+bool injected_oom(tc_ctx* ctx);
 tc_status cuda_status(tc_ctx* ctx, cudaError_t e, const char* what);
 tc_status err_bits_status(int bits);
 const char* err_bits_text(int bits);

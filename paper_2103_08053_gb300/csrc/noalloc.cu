@@ -9,7 +9,7 @@
 // scratch (queue counters, the warp-worker list and its descriptors, the
 // thread-block work items) in the file-scope array g_noalloc_scratch below.
 // The array is part of the library image: every GPU that loads the library
-// holds its NOALLOC_SCRATCH_BYTES (about 5.3 MB) until the process exits.
+// holds its kScratchBytes (about 5.8 MB) until the process exits.
 #include <mutex>
 
 #include "api_internal.h"
@@ -23,8 +23,10 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 constexpr int64_t kMaxN = TC_NOALLOC_MAX_N;
 constexpr int64_t kMaxM = TC_NOALLOC_MAX_M;
-constexpr int kItemNeighbors = 1024;  // the default tc_params.item_neighbors
-constexpr int64_t kItemCap = kMaxN + kMaxM / kItemNeighbors + 1;
+// This entry point always runs with the default parameters, so binning makes
+// at most item_capacity(n, m, default item_neighbors) thread-block work items
+// (one per large vertex plus one per item_neighbors of its out-edges).
+constexpr int64_t kItemCap = tcg::item_capacity(kMaxN, kMaxM, tcg::DEFAULT_ITEM_NEIGHBORS);
 
 // scratch layout: counters | warp-worker list | its descriptors | block items
 constexpr size_t kOffCtr = 0;

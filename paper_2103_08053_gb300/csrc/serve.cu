@@ -268,7 +268,9 @@ tc_status serve_start(tc_ctx* ctx) {
     ServeState* S = new (std::nothrow) ServeState();
     if (!S) return TC_ERR_OOM;
     void* p = nullptr;
-    tc_status s = cuda_status(ctx, cudaMalloc(&p, ctx->mem_budget), "cudaMalloc(serving arena)");
+    tc_status s = injected_oom(ctx)
+                      ? ctx_fail(ctx, TC_ERR_OOM, "cudaMalloc(serving arena): out of memory (injected by tc_inject_oom)")
+                      : cuda_status(ctx, cudaMalloc(&p, ctx->mem_budget), "cudaMalloc(serving arena)");
     if (!s) {
         S->arena_base = static_cast<unsigned char*>(p);
         S->arena.reset(ctx->mem_budget);

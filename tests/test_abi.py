@@ -61,6 +61,7 @@ def test_null_arguments_rejected_without_gpu(tc):
     assert tc.tc_count(None, None, None, None) == tc.TC_ERR_INVALID_ARG
     assert tc.tc_destroy(None) == tc.TC_OK
     assert tc.tc_default_params(None) == tc.TC_ERR_INVALID_ARG
+    assert tc.tc_inject_oom(None, 1) == tc.TC_ERR_INVALID_ARG
     assert isinstance(tc.tc_last_error(None), bytes)
 
 

@@ -3,12 +3,16 @@ uses (default parameters, one context).
 
 * the bench workload (RGG, 2^22 points, mean degree 64): whole count vs oracle;
 * R-MAT scale 16: whole count vs oracle;
-* R-MAT scale 26 with int64 offsets: per-vertex counts of a sample of vertices
-  vs the oracle's, and the per-vertex sum equal to the total;
-* the 4096-graph batched workload: batch vs per-graph loop vs oracle sample;
+* R-MAT scale 26 with int64 offsets: the total, W+ and every vertex's apex
+  count (by digest) against the oracle's, stored in tests/golden/rmat26.json,
+  plus the oriented offsets and a sample of apex counts against the oracle run
+  here;
+* the 4096-graph batched workload: every graph's count vs the oracle, and the
+  per-graph loop;
 * the dataset table's 3Dgrid row (a 464^3 periodic grid): |V|, |E| and the
   count (0) exactly as printed.
 """
+import hashlib
 import json
 import os
 
@@ -58,16 +62,25 @@ def test_rmat16_whole_count(T):
         assert c.count(*dev(g)) == oracle.count(g)
 
 
-def test_rmat26_sampled_per_vertex(T):
+def test_rmat26_whole_graph_against_the_oracle_golden(T):
+    # tests/golden/rmat26.json holds the oracle's whole-graph count, W+ and a
+    # digest of every vertex's apex count, written by tests/golden/make_rmat26.py
+    # (graph generator + CPU oracle only)
+    want = json.load(open(os.path.join(GOLDEN, "rmat26.json")))
     g = G.workload("rmat26")
+    assert (g.n, g.m, g.nnz) == (want["n"], want["m"], want["nnz"])
     assert g.nnz > 1_000_000_000
     with T.Context(0) as c:
-        n, rp, col = dev(g, 64)
+        n, rp, col = dev(g, 64)  # int64 row offsets, as the configuration states
         total = c.count(n, rp, col)
+        assert total == want["triangles"]
         d = c.orient(n, rp, col)
+        st = c.dag_stats(d)
+        assert st["wedges_plus"] == want["wedges_plus"] and st["max_out_degree"] == want["max_out_degree"]
         pv = torch.zeros(n, dtype=torch.int64, device="cuda")
         assert c.count_dag(d, per_vertex=pv) == total
-        assert int(pv.sum().item()) == total
+        got = pv.cpu().numpy().view(np.uint64)
+        assert hashlib.sha256(got.astype("<u8").tobytes()).hexdigest() == want["apex_sha256_le_u64"]
         od = oracle.orient(g)
         assert d.m == od.m == g.m
         dp, _ = d.tensors()
@@ -84,12 +97,12 @@ def test_rmat26_sampled_per_vertex(T):
 
 def test_batched_workload_4096(T):
     gs = G.batch(4, 4096)
+    want = oracle.count_many(gs)
     with T.Context(0) as c:
         tensors = [dev(g) for g in gs]
         counts = c.count_batch(tensors)
-        assert counts == [c.count(*t) for t in tensors]
-    for i in range(0, 4096, 128):
-        assert counts[i] == oracle.count(gs[i])
+        assert counts == want  # every graph of the batch against the oracle
+        assert [c.count(*t) for t in tensors] == want
 
 
 def test_3dgrid_dataset_row(T):

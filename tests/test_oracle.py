@@ -10,6 +10,7 @@ least one of them.
 import itertools
 import json
 import math
+from fractions import Fraction
 import os
 
 import numpy as np
@@ -339,3 +340,38 @@ def test_collision_stats_against_algorithm1_tables():
     assert oracle.collision_stats(dk, "mod32")[0] == 2          # 1 and 33 share bucket 1
     assert oracle.collision_stats(dk, "mult32")[0] <= 2
     assert oracle.collision_stats(oracle.orient(h), "mod32") == (1, 0)
+
+
+def knuth_multiplicative_bucket(x: int, B: int) -> int:
+    """Multiplicative hashing as Knuth defines it (TAOCP vol. 3, Sec. 6.4):
+    h(K) = floor(M * frac(K * A / w)) with word size w = 2^32, M = B buckets
+    and A the integer nearest w times the golden-ratio conjugate, taken
+    prime; computed with exact fractions."""
+    A = 2654435761
+    return int(B * (Fraction(x * A, 2 ** 32) % 1))
+
+
+def test_knuth_multiplier():
+    A = 2654435761
+    golden = (math.sqrt(5) - 1) / 2
+    assert abs(A - 2 ** 32 * golden) < 10
+    assert A % 2 and all(A % p for p in range(3, math.isqrt(A) + 1, 2))  # prime
+
+
+def test_collision_stats_mult32_against_algorithm1_tables():
+    # the "mult32" statistics are those of Algorithm 1's 32-bucket tables built
+    # with Knuth's multiplicative hash instead of x mod 32: the largest bucket
+    # load of any N+(u) and Eq. 2's phi from the same tables (levels >= d+:
+    # nothing overflows, so the loads are the unbounded ones)
+    for g in (G.rmat(9, 8, seed=93), G.rgg(600, 12.0, seed=94), G.complete(70)):
+        d = oracle.orient(g)
+        dp, dc = d.dag_ptr.tolist(), d.dag_col.tolist()
+        L = max(1, int(d.out_degrees().max()))
+        mx, phi = oracle.collision_stats(d, "mult32")
+        assert phi == alg1.phi_eq2(dp, dc, 32, L, knuth_multiplicative_bucket)
+        assert mx == max(alg1.hash_table_construction(dc[dp[u]:dp[u + 1]], 32, L,
+                                                      knuth_multiplicative_bucket).max_collision()
+                         for u in range(g.n) if dp[u + 1] > dp[u])
+        # and the mod32 statistics of the same graphs against the plain tables
+        mx0, phi0 = oracle.collision_stats(d, "mod32")
+        assert phi0 == alg1.phi_eq2(dp, dc, 32, L)
