@@ -1,11 +1,16 @@
 #!/usr/bin/env python3
 """Benchmark of the hot path: rank-by-degree orientation + vertex-centric
-hashed triangle counting, on the random-geometric-graph workload (2^22 points
-uniform in the unit square, radius set for mean degree 64, seed 2).
+hashed triangle counting (Algorithm 1 on N+), on the largest single-GPU
+workload: R-MAT scale 26 (67,108,864 vertices, edge factor 16, (a,b,c,d) =
+(0.57, 0.19, 0.19, 0.05), seed 3; 1.05 B undirected edges), int32 CSR with
+int64 row offsets.
 
 One step = one tc_count_async over the device-resident CSR: degree,
-orientation counts, scan, compaction, binning, hash build + probe, 64-bit
-reduction. Prints one JSON line (rank 0).
+orientation (row-local DAG), binning, hash build + probe, 64-bit reduction.
+Prints one JSON line (rank 0) with the main workload's TEPS, and beside it
+the random-geometric-graph workload (2^22 points, mean degree 64), the
+4096-graph batch, the served Poisson stream and the Sec. 3.3 / 4.1 / 4.2
+studies.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -33,19 +38,25 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(name="rgg-2^22-meandeg64-seed2", points_log2=22, mean_degree=64.0, seed=2)
-REF_SAMPLE = dict(name="rgg-2^20-meandeg64-seed2", points_log2=20, mean_degree=64.0, seed=2)
-# --workload: the other single-graph configurations, measured the same way
-OTHER_WORKLOADS = {
-    "rmat16": dict(name="rmat-s16-ef16-seed1", graph="rmat16"),
-    "rmat22": dict(name="rmat-s22-ef16-seed1", graph="rmat22"),
-    "rmat26": dict(name="rmat-s26-ef16-seed3", graph="rmat26"),
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+# single-graph workloads (--workload); the default is the largest one
+WORKLOADS = {
+    "rmat26": dict(name="rmat-s26-ef16-seed3", graph="rmat26", offset_bits=64, golden="rmat26.json",
+                   oracle_fraction=1 / 32),
+    "rgg22": dict(name="rgg-2^22-meandeg64-seed2", graph="rgg22", offset_bits=32, oracle_fraction=1.0),
+    "rmat16": dict(name="rmat-s16-ef16-seed1", graph="rmat16", offset_bits=32, oracle_fraction=1.0),
+    "rmat22": dict(name="rmat-s22-ef16-seed1", graph="rmat22", offset_bits=32, oracle_fraction=1.0),
 }
+DEFAULT_WORKLOAD = "rmat26"
+# the reference arm's per-step sample of the main workload's vertices
+REF_FRACTION = 1 / 256
 METRIC = "triangle-count TEPS"
 UNIT = "edges/s"
 FALLBACK_HBM_GBS = 6800.0
-PROFILE = os.path.join(ROOT, "profiles", "k_count_pack__rgg22.md")
 COUNT_SRC = os.path.join(ROOT, "paper_2103_08053_gb300", "csrc", "count.cu")
+# ncu summaries with the DRAM bytes of one counting step, per workload
+PROFILES = {"rgg22": os.path.join(ROOT, "profiles", "k_count_pack__rgg22.md"),
+            "rmat26": os.path.join(ROOT, "profiles", "counting__rmat26.md")}
 
 
 def log(*a):
@@ -58,9 +69,7 @@ def dist_env():
 
 def make_graph(spec):
     import graphgen as G
-    if "graph" in spec:
-        return G.workload(spec["graph"])
-    return G.rgg(1 << spec["points_log2"], spec["mean_degree"], seed=spec["seed"])
+    return G.workload(spec["graph"])
 
 
 # ------------------------------------------------------------------ clocks
@@ -135,12 +144,13 @@ def count_source_hash() -> str:
     return hashlib.sha256(open(COUNT_SRC, "rb").read()).hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the counting kernel from the committed ncu
-    summary, or None when the kernel source changed since the capture."""
+def profiled_traffic(key: str):
+    """DRAM bytes of the counting kernels per step from the committed ncu
+    summary of workload `key`, or None when there is none or the kernel
+    source changed since the capture."""
     try:
-        text = open(PROFILE).read()
-    except OSError:
+        text = open(PROFILES[key]).read()
+    except (OSError, KeyError):
         return None
     h = re.search(r"count\.cu sha256\[:16\]:\s*([0-9a-f]{16})", text)
     b = re.search(r"dram bytes per launch \(read\+write\):\s*([0-9.eE+]+)", text)
@@ -159,18 +169,16 @@ def count_phase_bytes(n: int, m: int, wplus: int) -> int:
 # ------------------------------------------------- batched and served graphs
 
 BATCH = dict(name="batch-4096-seed4", graphs=4096, seed=4)
-SERVE = dict(rate=2000.0, pool=256, pool_seed=5, big_fraction=0.01, big_scale=22, budget_gb=40, seed=5)
+SERVE = dict(rate=2000.0, big_fraction=0.01, big_scale=22, big_seeds=(5, 6, 7, 8), budget_gb=40, seed=5)
 
 
-def measure_batched(T, torch, dev, steps: int):
+def measure_batched(T, torch, dev, steps: int, gs):
     """tc_count_batch over the 4096-graph batch (CUDA-graph replay) against a
-    loop of tc_count over the same graphs, on the same GPU."""
+    loop of tc_count over the same graphs, on the same GPU; every graph's
+    count against the oracle's."""
     import numpy as np
 
-    import graphgen as G
-    t0 = time.time()
-    gs = G.batch(BATCH["seed"], BATCH["graphs"])
-    gen_s = time.time() - t0
+    import oracle
     tensors = [(g.n, torch.from_numpy(g.row_ptr.astype(np.int32)).to(dev),
                 torch.from_numpy(np.ascontiguousarray(g.col, dtype=np.int32)).to(dev)) for g in gs]
     edges = sum(g.m for g in gs)
@@ -191,46 +199,54 @@ def measure_batched(T, torch, dev, steps: int):
         t = time.perf_counter()
         loop = [c.count(n, rp, col) for n, rp, col in tensors]
         loop_s = time.perf_counter() - t
-    import oracle
-    sample = list(range(0, BATCH["graphs"], BATCH["graphs"] // 32))
-    want = [oracle.count(gs[i]) for i in sample]
+    t = time.time()
+    want = oracle.count_many(gs)
+    oracle_s = time.time() - t
     return {
-        "workload": BATCH["name"], "graphs": len(gs), "edges": edges, "generation_s": round(gen_s, 1),
+        "workload": BATCH["name"], "graphs": len(gs), "edges": edges,
         "ms_per_batch": batch_s * 1e3, "graphs_per_s": len(gs) / batch_s, "edges_per_s": edges / batch_s,
         "loop_graphs_per_s": len(gs) / loop_s, "speedup_vs_loop": loop_s / batch_s, "steps": steps,
         "autotuned": {k: tuned[k] for k in ("warp_max_out_degree", "warp_area_ints", "warp_min_buckets", "chunk",
                                              "warps_per_block", "item_neighbors")}, "tune_s": round(tune_s, 1),
-        "parity": {"batch_equals_loop": counts == loop,
-                   "oracle_sample": len(sample), "oracle_equal": [counts[i] for i in sample] == want},
+        "parity": {"batch_equals_loop": counts == loop, "oracle_graphs": len(want),
+                   "oracle_equal": counts == want, "oracle_s": round(oracle_s, 1)},
     }
 
 
-def measure_serving(T, torch, dev, seconds: float):
-    """Poisson arrivals (rate 2000/s) of requests drawn from the batched
-    distribution, 1% R-MAT scale-22 graphs, admitted under a 40 GB budget;
-    submit -> poll-ready latency and completed graphs/s."""
+def _percentiles(lat_ms):
+    import numpy as np
+    return {"p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+            "mean_ms": float(lat_ms.mean()), "max_ms": float(lat_ms.max())}
+
+
+def measure_serving(T, torch, dev, seconds: float, pool):
+    """Poisson arrivals (rate 2000/s) of triangle-count requests, 99 % drawn
+    uniformly from `pool` (independent draws of the batched distribution) and
+    1 % R-MAT scale-22 graphs, admitted under a 40 GB budget through
+    tc_submit_borrowed; submit -> poll-ready latency and completed graphs/s.
+    The same arrival trace is then run through a plain loop of tc_count_host,
+    one request after the other, each submitted at its arrival time."""
     import numpy as np
 
     import graphgen as G
-    pool = G.batch(SERVE["pool_seed"], SERVE["pool"])
-    big = [G.rmat(SERVE["big_scale"], 16, seed=SERVE["seed"] + i) for i in range(2)]
-    graphs = pool + big
+    big = [G.rmat(SERVE["big_scale"], 16, seed=s) for s in SERVE["big_seeds"]]
+    graphs = list(pool) + big
     pinned = []
     for g in graphs:
         rp = torch.from_numpy(g.row_ptr.astype(np.int32)).pin_memory()
         col = torch.from_numpy(np.ascontiguousarray(g.col, dtype=np.int32)).pin_memory()
-        pinned.append((g.n, rp, col, rp.numpy(), col.numpy()))
+        pinned.append((g.n, rp.numpy(), col.numpy(), rp, col))
     with T.Context(dev.index) as c:  # every graph counted alone first
-        alone = [c.count(n, rp.to(dev), col.to(dev)) for n, rp, col, _, _ in pinned]
+        alone = [c.count(n, rp.to(dev), col.to(dev)) for n, _, _, rp, col in pinned]
     rng = np.random.default_rng(SERVE["seed"])
     n_req = max(1, int(SERVE["rate"] * seconds))
     arrivals = np.cumsum(rng.exponential(1.0 / SERVE["rate"], n_req))
     pick = np.where(rng.random(n_req) < SERVE["big_fraction"], len(pool) + rng.integers(0, len(big), n_req),
                     rng.integers(0, len(pool), n_req))
-    with T.Context(dev.index, mem_budget=SERVE["budget_gb"] << 30) as c:
-        warm = c.submit_borrowed(pinned[0][0], pinned[0][3], pinned[0][4])  # starts the serving worker
-        c.drain()
-        assert c.poll(warm) == alone[0]
+    edges = sum(graphs[i].m for i in pick)
+
+    def trace_loop(submit, poll):
+        """Submit request i at arrivals[i]; collect completions as they come."""
         submit_t = np.zeros(n_req)
         done_t = np.zeros(n_req)
         result = [None] * n_req
@@ -240,29 +256,55 @@ def measure_serving(T, torch, dev, seconds: float):
         while nxt < n_req or outstanding:
             now = time.perf_counter() - t0
             while nxt < n_req and arrivals[nxt] <= now:
-                n, _, _, rp_np, col_np = pinned[pick[nxt]]
-                outstanding[c.submit_borrowed(n, rp_np, col_np)] = nxt
+                outstanding[submit(pick[nxt])] = nxt
                 submit_t[nxt] = time.perf_counter() - t0
                 nxt += 1
             for tk in list(outstanding):
-                v = c.poll(tk)
+                v = poll(tk)
                 if v is not None:
                     i = outstanding.pop(tk)
                     done_t[i] = time.perf_counter() - t0
                     result[i] = v
             if nxt < n_req and not outstanding:
                 time.sleep(max(0.0, min(arrivals[nxt] - (time.perf_counter() - t0), 0.001)))
+        return submit_t, done_t, result
+
+    with T.Context(dev.index, mem_budget=SERVE["budget_gb"] << 30) as c:
+        warm = c.submit_borrowed(pinned[0][0], pinned[0][1], pinned[0][2])  # starts the serving worker
+        c.drain()
+        assert c.poll(warm) == alone[0]
+        submit_t, done_t, result = trace_loop(lambda j: c.submit_borrowed(*pinned[j][:3]), c.poll)
     lat = (done_t - submit_t) * 1e3
-    edges = sum(graphs[i].m for i in pick)
     span = done_t.max() - submit_t.min()
+    served = {"graphs_per_s": n_req / span, "edges_per_s": edges / span, "span_s": span, **_percentiles(lat)}
+
+    # the plain per-graph call on the same trace: tc_count_host, one at a time
+    with T.Context(dev.index) as c:
+        for j in range(len(pool), len(graphs)):  # grow the workspace for the largest graphs
+            c.count_host(*pinned[j][:3])
+        done = {}
+
+        def submit_loop(j):
+            k = len(done)
+            done[k] = c.count_host(*pinned[j][:3])
+            return k
+
+        l_submit, l_done, l_result = trace_loop(submit_loop, lambda k: done.pop(k))
+    # a request of the loop waits for the ones before it: its latency runs from its arrival
+    l_lat = (l_done - arrivals) * 1e3
+    l_span = l_done.max() - arrivals.min()
     return {
         "arrival_rate_per_s": SERVE["rate"], "seconds": seconds, "requests": n_req,
         "big_requests": int((pick >= len(pool)).sum()), "budget_gb": SERVE["budget_gb"],
-        "graphs_per_s": n_req / span, "edges_per_s": edges / span,
-        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-        "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+        "draws": f"{len(pool)} independent draws of the batched distribution (uniform) + "
+                 f"{len(big)} R-MAT scale-{SERVE['big_scale']} graphs",
+        **served, "delivered_fraction": (n_req / span) / SERVE["rate"],
         "identical_to_alone": all(result[i] == alone[pick[i]] for i in range(n_req)),
         "submission": "tc_submit_borrowed from pinned host memory",
+        "loop": {"api": "tc_count_host per request, in arrival order", "graphs_per_s": n_req / l_span,
+                 "span_s": l_span, **_percentiles(l_lat),
+                 "identical_to_alone": all(l_result[i] == alone[pick[i]] for i in range(n_req))},
+        "served_vs_loop_graphs_per_s": (n_req / span) / (n_req / l_span),
     }
 
 
@@ -395,44 +437,33 @@ def reorder_profile_run(args):
 
 # -------------------------------------------------------------- the arms
 
-def run_gb300(args):
+def measure_graph(T, torch, dev, key, spec, g, steps, warmup, rank, world, dist, e2e_steps, clocks):
+    """Time `steps` device steps (tc_count_async) of graph g after `warmup`
+    untimed ones, then the end-to-end call (tc_count_host from pinned host
+    memory, copies inside the timed region). Returns the line's keys, the
+    context-side statistics and the counts."""
     import numpy as np
-    import torch
 
-    import paper_2103_08053_gb300 as T
-
-    rank, local_rank, world = dist_env()
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local_rank)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
-
-    t0 = time.time()
-    g = make_graph(WORKLOAD)
-    log(f"[rank {rank}] generated {WORKLOAD['name']}: n={g.n} m={g.m} in {time.time() - t0:.1f}s")
-    bits = 32 if g.nnz < 2 ** 31 else 64
+    from paper_2103_08053_gb300 import shard
+    bits = spec["offset_bits"]
+    if bits == 32 and g.nnz >= 2 ** 31:
+        bits = 64
     rp_h = g.row_ptr.astype(np.int32 if bits == 32 else np.int64)
     col_h = np.ascontiguousarray(g.col, dtype=np.int32)
     rp = torch.from_numpy(rp_h).to(dev)
     col = torch.from_numpy(col_h).to(dev)
-    from paper_2103_08053_gb300 import shard
-    params = dict(record_timing=1, **shard.shard_params(rank, world))
-    ctx = T.Context(local_rank, params=params)
+    ctx = T.Context(dev.index, params=dict(record_timing=1, **shard.shard_params(rank, world)))
     stream = torch.cuda.current_stream(dev)
 
     # exact statistics of the DAG (outside the timed region): W+ for the byte model
-    full = T.Context(local_rank)
-    dag = full.orient(g.n, rp, col)
-    st = full.dag_stats(dag)
-    dag.free()
-    full.close()
+    with T.Context(dev.index) as full:
+        dag = full.orient(g.n, rp, col)
+        st = full.dag_stats(dag)
+        dag.free()
 
     out = torch.zeros(1, dtype=torch.int64, device=dev)
     err = torch.zeros(1, dtype=torch.int32, device=dev)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         ctx.count_async(g.n, rp, col, out, err, stream=stream)
     torch.cuda.synchronize(dev)
     my_count = int(out.item())
@@ -441,35 +472,34 @@ def run_gb300(args):
     ctx.read_timing()  # drop warm-up timings
     launches0 = ctx.kernel_launches()
 
-    sampler = ClockSampler(local_rank)
+    sampler = ClockSampler(dev.index) if clocks else None
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
-    sampler.start()
-    time.sleep(0.3)
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         ctx.count_async(g.n, rp, col, out, err, stream=stream)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()
-    clocks = sampler.stop()
+    clk = sampler.stop() if sampler else None
     elapsed_ms = e0.elapsed_time(e1)
     launches = ctx.kernel_launches() - launches0
     tm = ctx.read_timing()
     total_count, elapsed_ms = shard.combine(my_count, elapsed_ms, device=dev)
-    ms_per_step = elapsed_ms / args.steps
-    value = g.m / (ms_per_step / 1e3)
+    ms_per_step = elapsed_ms / steps
 
     # end to end through the C ABI from pinned host memory: H2D of the CSR, the
     # whole path, D2H of the count, every step
     rp_pin = torch.from_numpy(rp_h).pin_memory()
     col_pin = torch.from_numpy(col_h).pin_memory()
-    e2e_steps = max(3, min(args.steps, 20))
-    for _ in range(max(3, args.warmup)):
+    for _ in range(3):
         ctx.count_host(g.n, rp_pin.numpy(), col_pin.numpy(), stream=stream)
     torch.cuda.synchronize(dev)
     if dist:
@@ -498,119 +528,254 @@ def run_gb300(args):
     h1.record(stream)
     torch.cuda.synchronize(dev)
     h2d_ms = h0.elapsed_time(h1) / 3
-    del rp_d, col_d
+    del rp_d, col_d, rp_pin, col_pin
     ctx.read_timing()
     ctx.close()
 
-    if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        return
-
     peak, peak_src = measured_hbm_peak()
-    count_ms = tm["count_ms"] / max(tm["calls"], 1)
+    calls = max(tm["calls"], 1)
+    count_ms = tm["count_ms"] / calls
     bytes_count = count_phase_bytes(g.n, g.m, st["wedges_plus"])
     achieved = bytes_count / (count_ms / 1e3) / 1e9
-    traffic = profiled_traffic() if WORKLOAD["name"] == "rgg-2^22-meandeg64-seed2" else None
-
-    result = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "strong", "vs_baseline": None, "dtype": "int32",
-        "data": "synthetic",
+    line = {
+        "value": g.m / (ms_per_step / 1e3), "ms_per_step": ms_per_step,
         "config": {
-            "workload": WORKLOAD["name"], "n": g.n, "m": g.m, "nnz": g.nnz, "offset_bits": bits,
+            "workload": spec["name"], "n": g.n, "m": g.m, "nnz": g.nnz, "offset_bits": bits,
             "triangles": total_count, "wedges_plus": st["wedges_plus"], "max_out_degree": st["max_out_degree"],
-            "bins": {"skip": st["n_skip"], "warp": st["n_warp"], "block": st["n_block"]},
+            "bins": {"skip": st["n_skip"], "warp": st["n_warp"], "block": st["n_block"],
+                     "wedges_plus_block": st["wedges_plus_block"]},
             "step": "tc_count_async: orientation + binning + hash build/probe + reduction, CSR resident in HBM",
             "l2": "no flush: inputs larger than L2 (col %.2f GB, DAG %.2f GB vs 129 MB)"
                   % (g.nnz * 4 / 1e9, (g.m + g.n) * 4 / 1e9),
             "parallelism": f"workload partition u % {world}" if world > 1 else "single GPU",
         },
-        "phases_ms": {"orient": tm["orient_ms"] / max(tm["calls"], 1), "bin": tm["bin_ms"] / max(tm["calls"], 1),
-                      "count": count_ms},
+        "phases_ms": {"orient": tm["orient_ms"] / calls, "bin": tm["bin_ms"] / calls, "count": count_ms},
         "roofline": {"kernel": "counting kernels (k_count_block + k_count_pack)", "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
-                     else "fallback 6.8 TB/s", "traffic": traffic,
+                     else "fallback 6.8 TB/s", "traffic": profiled_traffic(key),
                      "algorithmic_bytes_per_launch": bytes_count,
-                     "bytes_model": "4(n+1) + 12m + 4W+"},
+                     "bytes_model": "4(n+1) + 12m + 4W+ per counting step"},
         "e2e": {"value": g.m / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "stat": f"median of {e2e_steps} timed calls", "mean_ms_per_step": e2e_mean_ms,
                 "max_ms_per_step": max(e2e_each),
                 "h2d_bytes_per_step": int(rp_h.nbytes + col_h.nbytes), "d2h_bytes_per_step": 16,
-                "h2d_copy_ms": h2d_ms, "host_pinned": bool(col_pin.is_pinned()),
+                "h2d_copy_ms": h2d_ms, "host_pinned": True,
                 "count_equal_device": e2e_count == my_count,
                 "api": "tc_count_host (pinned host CSR)"},
         "gpu_launches": launches,
-        "clocks": clocks,
     }
-    # the batched, served and study sections and the CPU baseline are
-    # single-GPU measurements: a multi-rank run reports the sharded step only
-    single = world == 1
-    if args.batched and single:
-        result["batched"] = measure_batched(T, torch, dev, steps=args.batch_steps)
-    if args.serve_seconds > 0 and single:
-        result["serving"] = measure_serving(T, torch, dev, args.serve_seconds)
-    if args.reorder and single:
-        import numpy as np
+    if clk is not None:
+        line["clocks"] = clk
+    return line, (rp, col), total_count
 
-        import graphgen as G
-        big = G.rmat(22, 16, seed=5)
-        gs = {WORKLOAD["name"]: (g.n, rp, col),
-              "rmat-s22-ef16-seed5": (big.n, torch.from_numpy(big.row_ptr.astype(np.int32)).to(dev),
-                                      torch.from_numpy(np.ascontiguousarray(big.col, dtype=np.int32)).to(dev))}
-        result["reorder_study"] = measure_reorder(T, torch, dev, gs)
-    if args.ablation and single:
-        import numpy as np
 
-        import graphgen as G
-        small = G.workload("rmat16")
-        gs = {WORKLOAD["name"]: (g.n, rp, col),
-              "rmat-s16-ef16-seed1": (small.n, torch.from_numpy(small.row_ptr.astype(np.int32)).to(dev),
-                                      torch.from_numpy(np.ascontiguousarray(small.col, dtype=np.int32)).to(dev))}
-        result["ablation_study"] = measure_ablation(T, torch, dev, gs)
-    if not args.no_cpu_baseline and single:
-        import oracle
-        cores = oracle.max_threads()
+def bernoulli_sample(n: int, fraction: float, seed: int):
+    """Vertex ids, each kept independently with probability `fraction`. (An
+    arithmetic progression of ids would not do: R-MAT degrees depend on the
+    bits of an id, so ids equal modulo a power of two share a degree class.)"""
+    import numpy as np
+    return np.flatnonzero(np.random.default_rng(seed).random(n) < fraction).astype(np.int64)
+
+
+def oracle_baseline(g, fraction: float, seed: int = 7):
+    """The CPU oracle on the host cores: orientation of the whole graph, then
+    apex counts of every vertex (fraction 1) or of a Bernoulli sample of
+    `fraction` of the vertices, whose time divided by `fraction` estimates
+    the whole graph's. Returns (cpu_baseline, sampled vertices, their apex
+    counts, total or None)."""
+    import numpy as np
+
+    import oracle
+    cores = oracle.max_threads()
+    t = time.perf_counter()
+    d = oracle.orient(g)
+    t_orient = time.perf_counter() - t
+    if fraction >= 1.0:
         t = time.perf_counter()
-        want = oracle.count(g, threads=cores)
-        cpu_s = time.perf_counter() - t
-        result["cpu_baseline"] = {"value": g.m / cpu_s, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                  "sample": f"one oracle orientation + node-iterator count of the whole "
-                                            f"{WORKLOAD['name']} graph ({cpu_s:.1f} s)"}
-        result["parity"] = {"oracle": want, "gpu": total_count, "equal": want == total_count}
+        total, pv = oracle.count_dag(d, per_vertex=True, threads=cores)
+        t_count = time.perf_counter() - t
+        us, apex = np.arange(g.n), pv
+        est = t_orient + t_count
+        sample = (f"one oracle orientation + node-iterator count of the whole {g.name or 'graph'} "
+                  f"({est:.1f} s)")
+    else:
+        us = bernoulli_sample(g.n, fraction, seed)
+        t = time.perf_counter()
+        apex = oracle.count_dag_at(d, us, threads=cores)
+        t_count = time.perf_counter() - t
+        total = None
+        est = t_orient + t_count / fraction
+        sample = (f"oracle orientation of the whole graph ({t_orient:.1f} s) + apex counts of a Bernoulli "
+                  f"sample of the vertices with probability {fraction:g} ({len(us)} vertices, {t_count:.1f} s), "
+                  f"the count time divided by {fraction:g}: {est:.1f} s for the whole graph")
+    cb = {"value": g.m / est, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+          "seconds_whole_graph": est}
+    return cb, us, apex, total
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    import graphgen as G
+    import paper_2103_08053_gb300 as T
+
+    rank, local_rank, world = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    key = args.workload
+    spec = WORKLOADS[key]
+    single = world == 1
+
+    t0 = time.time()
+    g = make_graph(spec)
+    g.name = spec["name"]
+    log(f"[rank {rank}] generated {spec['name']}: n={g.n} m={g.m} in {time.time() - t0:.1f}s")
+    main, (rp, col), total = measure_graph(T, torch, dev, key, spec, g, args.steps, args.warmup, rank, world,
+                                           dist, e2e_steps=max(3, min(args.steps, args.e2e_steps)), clocks=True)
+    log(f"[rank {rank}] {spec['name']}: {main['ms_per_step']:.2f} ms per step")
+    result = {
+        "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        **{k: main[k] for k in ("config", "phases_ms", "roofline", "e2e", "gpu_launches", "clocks")},
+    }
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    # the CPU baseline, the parity checks, the second workload, the batched,
+    # served and study sections are single-GPU measurements: a multi-rank run
+    # reports the sharded step only
+    if single:
+        parity = {"gpu": total}
+        if spec.get("golden"):
+            want = json.load(open(os.path.join(GOLDEN, spec["golden"])))
+            parity.update({"golden": f"tests/golden/{spec['golden']}", "oracle": want["triangles"],
+                           "equal": want["triangles"] == total,
+                           "wedges_plus_equal": want["wedges_plus"] == main["config"]["wedges_plus"]})
+        if not args.no_cpu_baseline:
+            cb, us, apex, want_total = oracle_baseline(g, spec["oracle_fraction"])
+            result["cpu_baseline"] = cb
+            # the GPU's per-vertex apex counts at the oracle's sampled vertices
+            with T.Context(dev.index) as c:
+                d = c.orient(g.n, rp, col)
+                pv = torch.zeros(g.n, dtype=torch.int64, device=dev)
+                c.count_dag(d, per_vertex=pv)
+                d.free()
+            got = pv[torch.from_numpy(us).to(dev)].cpu().numpy().view(np.uint64)
+            del pv
+            parity["oracle_apex_vertices"] = int(len(us))
+            parity["oracle_apex_equal"] = bool(np.array_equal(got, apex))
+            if want_total is not None:
+                parity.update({"oracle": want_total, "equal": want_total == total})
+        result["parity"] = parity
+    del rp, col
+    torch.cuda.empty_cache()
+
+    if single and args.second and key != "rgg22":
+        s2 = WORKLOADS["rgg22"]
+        g2 = make_graph(s2)
+        g2.name = s2["name"]
+        line2, (rp2, col2), total2 = measure_graph(T, torch, dev, "rgg22", s2, g2, 50, 5, 0, 1, None, e2e_steps=10,
+                                                   clocks=False)
+        import oracle
+        t = time.perf_counter()
+        want2 = oracle.count(g2, threads=oracle.max_threads())
+        cpu2 = time.perf_counter() - t
+        line2["cpu_baseline"] = {"value": g2.m / cpu2, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+                                 "sample": f"one oracle orientation + node-iterator count of the whole graph "
+                                           f"({cpu2:.1f} s)"}
+        line2["parity"] = {"oracle": want2, "gpu": total2, "equal": want2 == total2}
+        result["rgg22"] = line2
+        studies_rgg = (g2, rp2, col2)
+    elif single and key == "rgg22":
+        studies_rgg = (g, *make_graph_tensors(torch, dev, g))
+    else:
+        studies_rgg = None
+
+    pool = None
+    if single and (args.batched or args.serve_seconds > 0):
+        t = time.time()
+        pool = G.batch(BATCH["seed"], BATCH["graphs"])
+        log(f"generated {BATCH['name']} in {time.time() - t:.1f}s")
+    if args.batched and single:
+        result["batched"] = measure_batched(T, torch, dev, args.batch_steps, pool)
+        result["batched"]["generation_s"] = round(time.time() - t, 1)
+    if args.serve_seconds > 0 and single:
+        result["serving"] = measure_serving(T, torch, dev, args.serve_seconds, pool)
+    del pool
+    if args.reorder and single and studies_rgg:
+        big = G.rmat(22, 16, seed=5)
+        gs = {WORKLOADS["rgg22"]["name"]: (studies_rgg[0].n, studies_rgg[1], studies_rgg[2]),
+              "rmat-s22-ef16-seed5": (big.n, *make_graph_tensors(torch, dev, big))}
+        result["reorder_study"] = measure_reorder(T, torch, dev, gs)
+    if args.ablation and single and studies_rgg:
+        small = G.workload("rmat16")
+        gs = {WORKLOADS["rgg22"]["name"]: (studies_rgg[0].n, studies_rgg[1], studies_rgg[2]),
+              WORKLOADS["rmat16"]["name"]: (small.n, *make_graph_tensors(torch, dev, small))}
+        result["ablation_study"] = measure_ablation(T, torch, dev, gs)
     if dist:
         dist.destroy_process_group()
     print(json.dumps(result), flush=True)
 
 
+def make_graph_tensors(torch, dev, g):
+    import numpy as np
+    return (torch.from_numpy(g.row_ptr.astype(np.int32)).to(dev),
+            torch.from_numpy(np.ascontiguousarray(g.col, dtype=np.int32)).to(dev))
+
+
 def run_reference(args):
+    """The oracle as it stands, on the host cores, on the main workload: the
+    whole graph is oriented once (timed), then every step counts the apex
+    triangles of a fresh systematic sample of REF_FRACTION of the vertices;
+    a step's value is the whole-graph TEPS it implies (orientation time +
+    sample time / REF_FRACTION)."""
     rank, _, world = dist_env()
     if rank != 0:
         return  # the CPU oracle runs once, on rank 0
+    import numpy as np
+
     import oracle
-    g = make_graph(REF_SAMPLE)
+    spec = WORKLOADS[args.workload]
+    g = make_graph(spec)
     # rank 0 alone does the work: all host cores, whatever OMP_NUM_THREADS
     # the launcher set for its ranks
     cores = max(oracle.max_threads(), len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity")
                 else (os.cpu_count() or 1))
-    for _ in range(args.warmup):
-        oracle.count(g, threads=cores)
-    times = []
-    for _ in range(args.steps):
+    t = time.perf_counter()
+    d = oracle.orient(g)
+    t_orient = time.perf_counter() - t
+    frac = REF_FRACTION if spec["oracle_fraction"] < 1 else 1.0
+    seeds = iter(range(11, 11 + args.warmup + args.steps))
+
+    def step():
+        us = bernoulli_sample(g.n, frac, next(seeds)) if frac < 1 else np.arange(g.n, dtype=np.int64)
         t = time.perf_counter()
-        oracle.count(g, threads=cores)
-        times.append(time.perf_counter() - t)
+        oracle.count_dag_at(d, us, threads=cores)
+        return time.perf_counter() - t
+
+    for _ in range(args.warmup):
+        step()
+    times = [step() for _ in range(args.steps)]
     ms = 1e3 * sum(times) / len(times)
-    value = g.m / (ms / 1e3)
-    sample = (f"one oracle orientation + node-iterator count per step of {REF_SAMPLE['name']} "
-              f"(same family as {WORKLOAD['name']}, 1/4 of its points), {cores} threads")
+    value = g.m / (t_orient + ms / 1e3 / frac)
+    sample = (f"oracle orientation of the whole {spec['name']} graph once ({t_orient:.1f} s), then per step the "
+              f"apex counts of a fresh Bernoulli sample of the vertices with probability {frac:g}, {cores} threads; "
+              f"value = m / (orientation + step time / {frac:g})")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": WORKLOAD["name"], "sample": REF_SAMPLE["name"], "n": g.n, "m": g.m},
+        "config": {"workload": spec["name"], "n": g.n, "m": g.m, "sample_fraction": frac,
+                   "orientation_s": t_orient},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -619,21 +784,24 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default=DEFAULT_WORKLOAD,
+                    help="graph of the timed steps (default: R-MAT scale 26 with int64 row offsets); the second "
+                         "workload, batched, serving and study sections use their own graphs")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="timed end-to-end calls (at most --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--second", type=int, default=1,
+                    help="1: also time the RGG 2^22 workload (rank 0) when it is not the main one")
     ap.add_argument("--batched", type=int, default=1, help="1: also time the 4096-graph batch (rank 0)")
     ap.add_argument("--batch-steps", type=int, default=5)
-    ap.add_argument("--workload", choices=["rgg22", *OTHER_WORKLOADS], default="rgg22",
-                    help="graph of the timed steps (default: the RGG 2^22 benchmark graph); the batched, serving "
-                         "and study sections always use their own workloads")
     ap.add_argument("--ablation", type=int, default=1,
                     help="1: also run the Sec. 3.3 (build/probe, edge-centric) and Sec. 4.2 (WC/SW/PC/VC) ablations (rank 0)")
     ap.add_argument("--reorder", type=int, default=1,
                     help="1: also run the Sec. 4.1 reordering study (rank 0)")
-    ap.add_argument("--serve-seconds", type=float, default=10.0,
-                    help="seconds of Poisson arrivals for the serving measurement (0: skip; the config is 60)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="seconds of Poisson arrivals for the serving measurement (0: skip)")
     ap.add_argument("--reorder-profile", default=None, metavar="GRAPH",
                     help="only run the Sec. 4.1 profiling sequence on this workload (e.g. rgg20, rmat21) and exit")
     ap.add_argument("--profile-hash-mode", type=int, choices=[0, 1], default=0,
@@ -644,9 +812,6 @@ def main():
         return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
-    if args.workload != "rgg22":
-        global WORKLOAD
-        WORKLOAD = OTHER_WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args)
     else:

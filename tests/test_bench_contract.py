@@ -16,7 +16,8 @@ def run(*args, env=None, timeout=600):
 
 def test_reference_arm_prints_one_contract_line():
     env = dict(os.environ, OMP_NUM_THREADS="1")  # as a launcher sets it: the arm must still use all cores
-    r = run("--impl", "reference", "--steps", "1", "--warmup", "3", env=env)
+    # a small workload keeps the CPU suite short; the default is R-MAT scale 26
+    r = run("--impl", "reference", "--workload", "rmat16", "--steps", "1", "--warmup", "3", env=env)
     assert r.returncode == 0, r.stderr
     lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
     assert len(lines) == 1
@@ -26,7 +27,7 @@ def test_reference_arm_prints_one_contract_line():
         assert key in d, key
     assert d["impl"] == "reference" and d["metric"] == "triangle-count TEPS" and d["unit"] == "edges/s"
     assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 3 and d["higher_is_better"] is True
-    assert d["config"]["workload"] == "rgg-2^22-meandeg64-seed2"
+    assert d["config"]["workload"] == "rmat-s16-ef16-seed1"
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] == (
         len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count())
@@ -42,5 +43,18 @@ def test_documented_flags_parse():
     r = run("--help", timeout=120)
     assert r.returncode == 0
     for flag in ("--gpus", "--steps", "--warmup", "--impl", "--workload", "--batched", "--serve-seconds",
-                 "--reorder", "--ablation", "--reorder-profile", "--profile-hash-mode", "--no-cpu-baseline"):
+                 "--reorder", "--ablation", "--reorder-profile", "--profile-hash-mode", "--no-cpu-baseline",
+                 "--second", "--e2e-steps"):
         assert flag in r.stdout, flag
+
+
+def test_default_workload_is_rmat26_with_int64_offsets():
+    sys.path.insert(0, ROOT)
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    w = b.WORKLOADS[b.DEFAULT_WORKLOAD]
+    assert w["name"] == "rmat-s26-ef16-seed3" and w["offset_bits"] == 64
+    golden = json.load(open(os.path.join(ROOT, "tests", "golden", w["golden"])))
+    assert golden["workload"] == w["name"] and golden["triangles"] > 2 ** 32
