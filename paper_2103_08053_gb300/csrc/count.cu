@@ -92,6 +92,9 @@ static_assert(VC_UNROLL == 4, "the bitmap owner path reads four window words at 
 #ifndef BLOCK_OVF
 #define BLOCK_OVF 1  // 1: thread-block tables mark overflowed buckets; only those send a search on
 #endif
+#ifndef BLOCK_OCTETS
+#define BLOCK_OCTETS 1  // 1: thread-block workers read 2-hop lists as 32-byte octets when dag_col is 32-byte aligned
+#endif
 #ifndef BLOCK_REHASH
 #define BLOCK_REHASH 1  // 1: a thread-block table with a displaced key is rebuilt with the next hash multiplier (up to 4)
 #endif
@@ -762,6 +765,84 @@ __device__ __forceinline__ uint32_t vc_range_quad(int s, int e, int nq, int tab,
     return hits;
 }
 
+// Octet variant of vc_range_quad (thread-block workers, dag_col 32-byte
+// aligned): lane i brings dag_col[s, e) with no octets (aligned 32-byte
+// groups of eight entries); the combined octet indices [skip, min(limit,
+// total)) are dealt one per lane per step, each read with one 256-bit load;
+// slots outside their list are masked. *done = octets processed.
+template <int HM, int SL, bool OVF, bool CHAIN>
+__device__ __forceinline__ uint32_t vc_range_oct(int s, int e, int no, int tab, int lgB, int skip, int limit,
+                                                 const int* sm, const int32_t* __restrict__ dag_col, int m, int lane,
+                                                 int* stage, int* done, unsigned mult) {
+    const unsigned nem = __ballot_sync(FULL, no > 0);
+    if (nem == 0) {
+        *done = 0;
+        return 0;
+    }
+    const int c = __popc(nem);
+    if (no > 0) {
+        const int p = __popc(nem & lanemask_lt(lane));
+        stage[p] = s;
+        stage[32 + p] = e;
+        stage[64 + p] = no;
+    }
+    __syncwarp();
+    const bool lst = lane < c;
+    const int cs = lst ? stage[lane] : 0;
+    const int ce = lst ? stage[32 + lane] : 0;
+    const int co = lst ? stage[64 + lane] : 0;
+    __syncwarp();
+    const int P = warp_incl_scan(co, lane);
+    const int total = __shfl_sync(FULL, P, 31);
+    const int end = total < limit ? total : limit;
+    const int Pex = P - co;
+    const int obias = (cs >> 3) - Pex;
+    const unsigned le = lanemask_le(lane);
+    const int mask = (1 << lgB) - 1;
+    uint32_t hits = 0;
+    for (int base = skip; base < end; base += 32) {
+        const int o = vc_owner(base, P, Pex, lst, le) & 31;
+        const int ob = __shfl_sync(FULL, obias, o);
+        const int so = __shfl_sync(FULL, cs, o);
+        const int eo = __shfl_sync(FULL, ce, o);
+        const int f = base + lane;
+        const int x0 = 8 * (ob + f);  // dag_col index of the octet's first slot
+        Octet k;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) k.v[j] = NOKEY;
+        int lo = 8, hi = 0;
+        if (f < end) {
+            lo = so - x0;
+            hi = eo - x0;
+            if (x0 + 7 < m) {
+                k = ld_octet(dag_col + x0);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 7; ++j)
+                    if (x0 + j < m) k.v[j] = __ldg(dag_col + x0 + j);
+            }
+        }
+        int more = 0;  // bit j: slot j's bucket may have sent its key on and did not match
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (j >= lo && j < hi) {
+                const int h = bucket_of<HM>(k.v[j], lgB, mult);
+                const Bucket<SL> b = Bucket<SL>::at(sm, tab, h);
+                const int hit = bucket_match<SL, OVF>(b, k.v[j]);
+                hits += hit;
+                if (CHAIN) more |= (!hit && bucket_more<SL, OVF>(b)) << j;
+            }
+        }
+        if (CHAIN && __any_sync(FULL, more)) {
+            for (int j = 0; j < 8; ++j)
+                if ((more >> j) & 1)
+                    hits += probe_chain<SL, OVF>(sm, tab, mask, bucket_of<HM>(k.v[j], lgB, mult), k.v[j]);
+        }
+    }
+    *done = end > skip ? end - skip : 0;
+    return hits;
+}
+
 // ---- intra-vertex workload balancing alternatives (Sec. 4.2) -----------------
 // The paper compares virtual combination with three other ways of spreading
 // the 2-hop lists N+(v), v in N+(u), over a warp's lanes. They are kept here
@@ -1141,7 +1222,10 @@ __global__ void __launch_bounds__(1024, 1)
         if ((int)threadIdx.x < cnt)
             list_bounds(__ldg(dag_col + a + nb0 + threadIdx.x), dag_ptr, dag_bnd, n, ctr, ls, ll);
         // quad path: the prefix counts the quads each list spans
-        const int units = (quad && ll > 0) ? ((ls + ll + 3) >> 2) - (ls >> 2) : ll;
+        // quad == 1: the prefix counts the quads each list spans; quad == 2: octets
+        const int units = ll <= 0 ? 0
+                          : quad == 2 ? ((ls + ll + 7) >> 3) - (ls >> 3)
+                          : quad      ? ((ls + ll + 3) >> 2) - (ls >> 2) : ll;
         const int wi = warp_incl_scan(units, lane);
         if (lane == 31) s_wsum[w] = wi;
         __syncthreads();
@@ -1198,7 +1282,7 @@ __global__ void __launch_bounds__(1024, 1)
             if (timing) cyc_b += t_probe - t_build;
             // combined units (quads or keys) per piece: about 2 pieces per warp
             // (pieces are equal, so that balances), at least one 32-unit window
-            const int unit_min = quad ? PIECE / 4 : PIECE;
+            const int unit_min = quad == 2 ? PIECE / 8 : quad ? PIECE / 4 : PIECE;
             int piece = (W + 2 * nw - 1) / (2 * nw);
             piece = BLOCK_ADAPTIVE_PIECE ? (piece < 32 ? 32 : (piece + 31) & ~31) : unit_min;
             for (;;) {
@@ -1219,7 +1303,17 @@ __global__ void __launch_bounds__(1024, 1)
                     const int sj = j < cnt ? S[j] : 0;
                     const int base_flat = j0 ? LP[j0 - 1] : 0;
                     int done = 0;
-                    if (quad && !chained) {
+                    if (quad == 2) {
+                        const int ej = j < cnt ? E[j] : 0;
+                        if (!chained)
+                            h += vc_range_oct<HM, BLOCK_SLOTS, false, false>(sj, ej, uj, table_off, lgB,
+                                                                             F - base_flat, F1 - base_flat, smem,
+                                                                             dag_col, m, lane, stage, &done, mult);
+                        else
+                            h += vc_range_oct<HM, BLOCK_SLOTS, BLOCK_OVF, true>(sj, ej, uj, table_off, lgB,
+                                                                                F - base_flat, F1 - base_flat, smem,
+                                                                                dag_col, m, lane, stage, &done, mult);
+                    } else if (quad && !chained) {
                         const int ej = j < cnt ? E[j] : 0;
                         h += vc_range_quad<HM, BLOCK_SLOTS, false, false>(sj, ej, uj, table_off, lgB, F - base_flat,
                                                                           F1 - base_flat, smem, dag_col, m, lane,
@@ -1571,9 +1665,11 @@ cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t
     // shape, known on the device after binning, picks the one that runs
     const int pack_quad =
         (quad && PACK_OCTETS && cfg.balance == TC_BALANCE_VC && ((uintptr_t)dag_col & 31) == 0) ? 2 : quad;
+    // thread-block workers read 32-byte octets when dag_col is 32-byte aligned
+    const int block_quad = (quad && BLOCK_OCTETS && ((uintptr_t)dag_col & 31) == 0) ? 2 : quad;
     block_kernel(cfg.hash_mode)<<<cfg.block_grid, cfg.block_threads, cfg.block_smem_bytes, st>>>(
         dag_ptr, dag_col, items, per_vertex, ctr, (int)n, table_off, count_block_part_max(cfg), cfg.item_neighbors,
-        quad, cfg.cycle_timing, dag_bnd);
+        block_quad, cfg.cycle_timing, dag_bnd);
     pack_kernel(per_vertex != nullptr, cfg.hash_mode, cfg.balance)<<<cfg.warp_grid, cfg.warps_per_block * 32,
                                                                    pack_smem_bytes(cfg), st>>>(
         dag_ptr, dag_col, warp_desc, warp_list, per_vertex, ctr, (int)n, cfg.warp_area_ints,
