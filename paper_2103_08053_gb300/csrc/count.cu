@@ -114,6 +114,17 @@ constexpr int OVF_BIT = (int)0x80000000u;
 __device__ __forceinline__ unsigned lanemask_le(int lane) { return (2u << lane) - 1u; }
 __device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
 
+// Slots of a group of W <= 8 consecutive dag_col entries that belong to a
+// list: with the list at [x0 + lo, x0 + hi) relative to the group's first
+// entry x0, bit j is set iff lo <= j < hi. Computed once per group, so the
+// group's slots are all probed without per-slot range tests and the hits
+// are counted as popc(match bits & mask).
+template <int W>
+__device__ __forceinline__ unsigned slot_mask(int lo, int hi) {
+    const unsigned a = (unsigned)min(max(lo, 0), W), b = (unsigned)min(max(hi, 0), W);
+    return (((1u << b) - 1u) >> a) << a;
+}
+
 __device__ __forceinline__ int warp_incl_scan(int v, int lane) {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -543,14 +554,13 @@ __device__ __forceinline__ uint32_t vc_pack_quad(int s, int l, int td, const int
             const int lg = (kd[q] >> 16) & 31;
             const int tab = kd[q] & 0xffff;
             const int key[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
-            int hq = 0;
+            unsigned mb = 0;  // bit j: slot j matched (every slot is probed; the mask keeps the list's)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                if (j >= lo[q] && j < hi[q]) {
-                    const int h = bucket_of<HM>(key[j], lg, mult);
-                    hq += Bucket<SL>::at(sm, tab, h).match(key[j]);
-                }
+                const int h = bucket_of<HM>(key[j], lg, mult);
+                mb |= (unsigned)Bucket<SL>::at(sm, tab, h).match(key[j]) << j;
             }
+            const int hq = __popc(mb & slot_mask<4>(lo[q], hi[q]));
             hits += hq;
             if (SLOT_HITS) {
                 const int sl = (kd[q] >> 21) & 31;
@@ -653,14 +663,13 @@ __device__ __forceinline__ uint32_t vc_pack_oct(int s, int l, int td, const int*
         }
         const int lg = (kd >> 16) & 31;
         const int tab = kd & 0xffff;
-        int hq = 0;
+        unsigned mb = 0;  // bit j: slot j matched (every slot is probed; the mask keeps the list's)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            if (j >= lo && j < hi) {
-                const int h = bucket_of<HM>(k.v[j], lg, mult);
-                hq += Bucket<SL>::at(sm, tab, h).match(k.v[j]);
-            }
+            const int h = bucket_of<HM>(k.v[j], lg, mult);
+            mb |= (unsigned)Bucket<SL>::at(sm, tab, h).match(k.v[j]) << j;
         }
+        const int hq = __popc(mb & slot_mask<8>(lo, hi));
         hits += hq;
         if (SLOT_HITS) {
             const int sl = (kd >> 21) & 31;
