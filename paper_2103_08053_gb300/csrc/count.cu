@@ -96,11 +96,17 @@ static_assert(VC_UNROLL == 4, "the bitmap owner path reads four window words at 
 #define BLOCK_OCTETS 1  // 1: thread-block workers read 2-hop lists as 32-byte octets when dag_col is 32-byte aligned
 #endif
 #ifndef BLOCK_REHASH
-#define BLOCK_REHASH 1  // 1: a thread-block table with a displaced key is rebuilt with the next hash multiplier (up to 4)
+#define BLOCK_REHASH 3  // rebuilds of a thread-block table with a displaced key, each with the next hash multiplier (0..3)
 #endif
 #ifndef BLOCK_SPARSE
 #define BLOCK_SPARSE 0  // log2 of the extra bucket factor of thread-block tables (B = nextpow2(part) << this)
 #endif
+
+// Dynamic shared memory of the counting kernels. The device helpers index
+// this array with int offsets (shared-space addressing) instead of taking
+// generic pointers into it, so that no access has to convert a generic
+// address to a shared one.
+extern __shared__ int g_smem[];
 
 constexpr int STAGE_INTS = 224;        // warp workers: 4 x 32 compaction lanes | 32 slot hits | 64-word bitmap
 constexpr int BLOCK_STAGE_INTS = 128;  // thread-block workers: 4 x 32 compaction lanes
@@ -181,15 +187,15 @@ __device__ __forceinline__ int bucket_of(int w, int lgB, unsigned mult = kHashMu
 // of the length words; B = 2^lgB. Lengths count claims (<= keys <= 255).
 // Returns 1 when the key did not fit its home bucket (the table overflowed).
 template <int HM, int SL = 4>
-__device__ __forceinline__ int insert_b4(int* sm, int tab, int lenw, int lgB, int w, unsigned mult) {
+__device__ __forceinline__ int insert_b4(int tab, int lenw, int lgB, int w, unsigned mult) {
     const int mask = (1 << lgB) - 1;
     int h = bucket_of<HM>(w, lgB, mult);
     for (int s = 0; s <= mask; ++s) {
         const int sh = 8 * (h & 3);
-        const unsigned old = atomicAdd(reinterpret_cast<unsigned*>(sm + lenw + (h >> 2)), 1u << sh);
+        const unsigned old = atomicAdd(reinterpret_cast<unsigned*>(g_smem + lenw + (h >> 2)), 1u << sh);
         const int slot = (old >> sh) & 0xff;
         if (slot < SL) {
-            sm[tab + SL * h + slot] = w;
+            g_smem[tab + SL * h + slot] = w;
             return s > 0;
         }
         h = (h + 1) & mask;
@@ -203,19 +209,19 @@ __device__ __forceinline__ int insert_b4(int* sm, int tab, int lenw, int lgB, in
 // 2^16 - 1 keys, so a length never carries into its neighbour).
 // Returns 1 when the key did not fit its home bucket.
 template <int HM, int SL = 4>
-__device__ __forceinline__ int insert_b4w(int* sm, int tab, int lenw, int lgB, int w, unsigned mult) {
+__device__ __forceinline__ int insert_b4w(int tab, int lenw, int lgB, int w, unsigned mult) {
     const int mask = (1 << lgB) - 1;
     int h = bucket_of<HM>(w, lgB, mult);
     for (int s = 0; s <= mask; ++s) {
         int slot;
         if (SL == 4) {
-            slot = atomicAdd(sm + lenw + h, 1);
+            slot = atomicAdd(g_smem + lenw + h, 1);
         } else {
             const int sh = 16 * (h & 1);
-            slot = (int)((atomicAdd(reinterpret_cast<unsigned*>(sm + lenw + (h >> 1)), 1u << sh) >> sh) & 0xffffu);
+            slot = (int)((atomicAdd(reinterpret_cast<unsigned*>(g_smem + lenw + (h >> 1)), 1u << sh) >> sh) & 0xffffu);
         }
         if (slot < SL) {
-            sm[tab + SL * h + slot] = w;
+            g_smem[tab + SL * h + slot] = w;
             return s > 0;
         }
         h = (h + 1) & mask;
@@ -235,8 +241,8 @@ struct Bucket;
 template <>
 struct Bucket<4> {
     int4 q;
-    __device__ __forceinline__ static Bucket at(const int* sm, int tab, int h) {
-        return {*reinterpret_cast<const int4*>(sm + tab + 4 * h)};
+    __device__ __forceinline__ static Bucket at(int tab, int h) {
+        return {*reinterpret_cast<const int4*>(g_smem + tab + 4 * h)};
     }
     __device__ __forceinline__ int match(int w) const { return match4(q, w); }
     __device__ __forceinline__ bool full() const { return q.w != EMPTY; }
@@ -249,8 +255,8 @@ struct Bucket<4> {
 template <>
 struct Bucket<2> {
     int2 q;
-    __device__ __forceinline__ static Bucket at(const int* sm, int tab, int h) {
-        return {*reinterpret_cast<const int2*>(sm + tab + 2 * h)};
+    __device__ __forceinline__ static Bucket at(int tab, int h) {
+        return {*reinterpret_cast<const int2*>(g_smem + tab + 2 * h)};
     }
     __device__ __forceinline__ int match(int w) const { return (q.x == w) | (q.y == w); }
     __device__ __forceinline__ bool full() const { return q.y != EMPTY; }
@@ -275,15 +281,26 @@ __device__ __forceinline__ bool bucket_more(const Bucket<SL>& b) {
 // Algorithm 1 linearSearch continued past bucket h0 (slow path): the
 // successor buckets in order, while bucket_more says a key may lie further on.
 template <int SL, bool OVF = false>
-__device__ __noinline__ int probe_chain(const int* sm, int tab, int mask, int h0, int w) {
+__device__ __noinline__ int probe_chain(int tab, int mask, int h0, int w) {
     int h = (h0 + 1) & mask;
     for (int s = 0; s < mask; ++s) {
-        const Bucket<SL> b = Bucket<SL>::at(sm, tab, h);
+        const Bucket<SL> b = Bucket<SL>::at(tab, h);
         const int hit = bucket_match<SL, OVF>(b, w);
         if (hit | !bucket_more<SL, OVF>(b)) return hit;
         h = (h + 1) & mask;
     }
     return 0;
+}
+
+// The next step of a search for w whose home bucket h0 may have sent it on:
+// bucket h0 + 1, inline; only a search that must go further calls probe_chain.
+template <int SL, bool OVF>
+__device__ __forceinline__ int probe_next(int tab, int mask, int h0, int w) {
+    const int h = (h0 + 1) & mask;
+    const Bucket<SL> b = Bucket<SL>::at(tab, h);
+    const int hit = bucket_match<SL, OVF>(b, w);
+    if (hit | !bucket_more<SL, OVF>(b)) return hit;
+    return probe_chain<SL, OVF>(tab, mask, h, w);
 }
 
 // After a thread-block table is built: mark every bucket that received more
@@ -293,10 +310,11 @@ __device__ __noinline__ int probe_chain(const int* sm, int tab, int mask, int h0
 // for SL = 4, 16-bit halves for SL = 2). Called by all threads of the block
 // between two barriers.
 template <int SL>
-__device__ __forceinline__ void mark_overflow(int* sm, int tab, int lenw, int nbuckets) {
+__device__ __forceinline__ void mark_overflow(int tab, int lenw, int nbuckets) {
     for (int t = threadIdx.x; t < nbuckets; t += blockDim.x) {
-        const int claims = SL == 4 ? sm[lenw + t] : (int)(((unsigned)sm[lenw + (t >> 1)] >> (16 * (t & 1))) & 0xffffu);
-        if (claims > SL) sm[tab + SL * t + SL - 1] |= OVF_BIT;
+        const int claims =
+            SL == 4 ? g_smem[lenw + t] : (int)(((unsigned)g_smem[lenw + (t >> 1)] >> (16 * (t & 1))) & 0xffffu);
+        if (claims > SL) g_smem[tab + SL * t + SL - 1] |= OVF_BIT;
     }
 }
 
@@ -307,20 +325,20 @@ __device__ __forceinline__ void mark_overflow(int* sm, int tab, int lenw, int nb
 // overflow chain. NOKEY lanes never match.
 template <bool SLOT_HITS, int HM, int SL, bool OVF>
 __device__ __forceinline__ uint32_t probe4(const int (&key)[VC_UNROLL], const int (&kt)[VC_UNROLL],
-                                           const int (&km)[VC_UNROLL], const int* sm, int* stage, unsigned mult) {
+                                           const int (&km)[VC_UNROLL], int stage, unsigned mult) {
     uint32_t hits = 0;
 #pragma unroll
     for (int q = 0; q < VC_UNROLL; ++q) {
         const int lg = km[q] & 0xffff;
         const int h = bucket_of<HM>(key[q], lg, mult);
-        const Bucket<SL> b = Bucket<SL>::at(sm, kt[q], h);
+        const Bucket<SL> b = Bucket<SL>::at(kt[q], h);
         int hit = bucket_match<SL, OVF>(b, key[q]);
         const bool more = key[q] >= 0 && !hit && bucket_more<SL, OVF>(b);
         if (__any_sync(FULL, more)) {
-            if (more) hit = probe_chain<SL, OVF>(sm, kt[q], (1 << lg) - 1, h, key[q]);
+            if (more) hit = probe_chain<SL, OVF>(kt[q], (1 << lg) - 1, h, key[q]);
         }
         hits += hit;
-        if (SLOT_HITS && hit) atomicAdd(&stage[128 + (km[q] >> 16)], 1);
+        if (SLOT_HITS && hit) atomicAdd(&g_smem[stage + 128 + (km[q] >> 16)], 1);
     }
     return hits;
 }
@@ -336,8 +354,8 @@ __device__ __forceinline__ uint32_t probe4(const int (&key)[VC_UNROLL], const in
 // Returns the hits; *done = number of combined indices processed.
 template <bool SLOT_HITS, int HM, int SL = 4, bool OVF = false>
 __device__ __forceinline__ uint32_t vc_range_b4(int s, int l, int tab, int lgB, int slot, int skip, int limit,
-                                                const int* sm, const int32_t* __restrict__ dag_col, int lane,
-                                                int* stage, int* done, unsigned mult = kHashMult0) {
+                                                const int32_t* __restrict__ dag_col, int lane,
+                                                int stage, int* done, unsigned mult = kHashMult0) {
     const unsigned nem = __ballot_sync(FULL, l > 0);
     if (nem == 0) {
         *done = 0;
@@ -346,17 +364,17 @@ __device__ __forceinline__ uint32_t vc_range_b4(int s, int l, int tab, int lgB, 
     const int c = __popc(nem);
     if (l > 0) {
         const int p = __popc(nem & lanemask_lt(lane));
-        stage[p] = s;
-        stage[32 + p] = l;
-        stage[64 + p] = tab;
-        stage[96 + p] = lgB | (slot << 16);
+        g_smem[stage + p] = s;
+        g_smem[stage + 32 + p] = l;
+        g_smem[stage + 64 + p] = tab;
+        g_smem[stage + 96 + p] = lgB | (slot << 16);
     }
     __syncwarp();
     const bool lst = lane < c;
-    const int cs = lst ? stage[lane] : 0;
-    const int cl = lst ? stage[32 + lane] : 0;
-    const int ctab = stage[64 + (lst ? lane : 0)];  // lanes past the lists alias list 0's table
-    const int cms = lst ? stage[96 + lane] : 0;
+    const int cs = lst ? g_smem[stage + lane] : 0;
+    const int cl = lst ? g_smem[stage + 32 + lane] : 0;
+    const int ctab = g_smem[stage + 64 + (lst ? lane : 0)];  // lanes past the lists alias list 0's table
+    const int cms = lst ? g_smem[stage + 96 + lane] : 0;
     __syncwarp();
     const int P = warp_incl_scan(cl, lane);
     const int total = __shfl_sync(FULL, P, 31);
@@ -377,7 +395,7 @@ __device__ __forceinline__ uint32_t vc_range_b4(int s, int l, int tab, int lgB, 
             const int f = b + lane;
             key[q] = (f < end) ? __ldg(dag_col + bo + f) : NOKEY;
         }
-        hits += probe4<SLOT_HITS, HM, SL, OVF>(key, kt, km, sm, stage, mult);
+        hits += probe4<SLOT_HITS, HM, SL, OVF>(key, kt, km, stage, mult);
     }
     *done = end > skip ? end - skip : 0;
     return hits;
@@ -393,23 +411,23 @@ __device__ __forceinline__ uint32_t vc_range_b4(int s, int l, int tab, int lgB, 
 // chunks use vc_owner.
 constexpr int BITMAP_WORDS = 64;  // 2048 combined indices
 template <bool SLOT_HITS, int HM, int SL>
-__device__ __forceinline__ uint32_t vc_pack_fast(int s, int l, int td, const int* sm,
-                                                 const int32_t* __restrict__ dag_col, int lane, int* stage,
+__device__ __forceinline__ uint32_t vc_pack_fast(int s, int l, int td,
+                                                 const int32_t* __restrict__ dag_col, int lane, int stage,
                                                  unsigned mult) {
     const unsigned nem = __ballot_sync(FULL, l > 0);
     if (nem == 0) return 0;
     const int c = __popc(nem);
     if (l > 0) {
         const int p = __popc(nem & lanemask_lt(lane));
-        stage[p] = s;
-        stage[32 + p] = l;
-        stage[64 + p] = td;
+        g_smem[stage + p] = s;
+        g_smem[stage + 32 + p] = l;
+        g_smem[stage + 64 + p] = td;
     }
     __syncwarp();
     const bool lst = lane < c;
-    const int cs = lst ? stage[lane] : 0;
-    const int cl = lst ? stage[32 + lane] : 0;
-    const int ctd = stage[64 + (lst ? lane : 0)];  // lanes past the lists alias list 0's table
+    const int cs = lst ? g_smem[stage + lane] : 0;
+    const int cl = lst ? g_smem[stage + 32 + lane] : 0;
+    const int ctd = g_smem[stage + 64 + (lst ? lane : 0)];  // lanes past the lists alias list 0's table
     __syncwarp();
     const int P = warp_incl_scan(cl, lane);
     const int total = __shfl_sync(FULL, P, 31);
@@ -417,7 +435,7 @@ __device__ __forceinline__ uint32_t vc_pack_fast(int s, int l, int td, const int
     const int bias = cs - Pex;
     const unsigned le = lanemask_le(lane);
     uint32_t hits = 0;
-    unsigned* bm = reinterpret_cast<unsigned*>(stage + 160);
+    unsigned* bm = reinterpret_cast<unsigned*>(g_smem + stage + 160);
     const bool use_bm = total <= 32 * BITMAP_WORDS;
     if (use_bm) {
         bm[lane] = 0u;
@@ -450,9 +468,9 @@ __device__ __forceinline__ uint32_t vc_pack_fast(int s, int l, int td, const int
 #pragma unroll
         for (int q = 0; q < VC_UNROLL; ++q) {
             const int h = bucket_of<HM>(key[q], (kd[q] >> 16) & 31, mult);
-            const int hit = Bucket<SL>::at(sm, kd[q] & 0xffff, h).match(key[q]);
+            const int hit = Bucket<SL>::at(kd[q] & 0xffff, h).match(key[q]);
             hits += hit;
-            if (SLOT_HITS && hit) atomicAdd(&stage[128 + ((kd[q] >> 21) & 31)], 1);
+            if (SLOT_HITS && hit) atomicAdd(&g_smem[stage + 128 + ((kd[q] >> 21) & 31)], 1);
         }
     }
     return hits;
@@ -471,23 +489,23 @@ __device__ __forceinline__ uint32_t vc_pack_fast(int s, int l, int td, const int
 // vc_owner.
 constexpr int QUAD_UNROLL = 2;  // quads in flight per lane
 template <bool SLOT_HITS, int HM, int SL>
-__device__ __forceinline__ uint32_t vc_pack_quad(int s, int l, int td, const int* sm,
-                                                 const int32_t* __restrict__ dag_col, int m, int lane, int* stage,
+__device__ __forceinline__ uint32_t vc_pack_quad(int s, int l, int td,
+                                                 const int32_t* __restrict__ dag_col, int m, int lane, int stage,
                                                  unsigned mult) {
     const unsigned nem = __ballot_sync(FULL, l > 0);
     if (nem == 0) return 0;
     const int c = __popc(nem);
     if (l > 0) {
         const int p = __popc(nem & lanemask_lt(lane));
-        stage[p] = s;
-        stage[32 + p] = s + l;
-        stage[64 + p] = td;
+        g_smem[stage + p] = s;
+        g_smem[stage + 32 + p] = s + l;
+        g_smem[stage + 64 + p] = td;
     }
     __syncwarp();
     const bool lst = lane < c;
-    const int cs = lst ? stage[lane] : 0;
-    const int ce = lst ? stage[32 + lane] : 0;
-    const int ctd = stage[64 + (lst ? lane : 0)];  // lanes past the lists alias list 0's table
+    const int cs = lst ? g_smem[stage + lane] : 0;
+    const int ce = lst ? g_smem[stage + 32 + lane] : 0;
+    const int ctd = g_smem[stage + 64 + (lst ? lane : 0)];  // lanes past the lists alias list 0's table
     __syncwarp();
     const int nq = lst ? ((ce + 3) >> 2) - (cs >> 2) : 0;
     const int P = warp_incl_scan(nq, lane);
@@ -496,7 +514,7 @@ __device__ __forceinline__ uint32_t vc_pack_quad(int s, int l, int td, const int
     const int qbias = (cs >> 2) - Pex;  // global quad index of combined quad f of this list: qbias + f
     const unsigned le = lanemask_le(lane);
     uint32_t hits = 0;
-    unsigned* bm = reinterpret_cast<unsigned*>(stage + 160);
+    unsigned* bm = reinterpret_cast<unsigned*>(g_smem + stage + 160);
     const bool use_bm = total <= 32 * BITMAP_WORDS;
     if (use_bm) {
         bm[lane] = 0u;
@@ -558,14 +576,14 @@ __device__ __forceinline__ uint32_t vc_pack_quad(int s, int l, int td, const int
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int h = bucket_of<HM>(key[j], lg, mult);
-                mb |= (unsigned)Bucket<SL>::at(sm, tab, h).match(key[j]) << j;
+                mb |= (unsigned)Bucket<SL>::at(tab, h).match(key[j]) << j;
             }
             const int hq = __popc(mb & slot_mask<4>(lo[q], hi[q]));
             hits += hq;
             if (SLOT_HITS) {
                 const int sl = (kd[q] >> 21) & 31;
                 if (sl != run_slot) {
-                    if (run_hits) atomicAdd(&stage[128 + run_slot], run_hits);
+                    if (run_hits) atomicAdd(&g_smem[stage + 128 + run_slot], run_hits);
                     run_slot = sl;
                     run_hits = 0;
                 }
@@ -573,7 +591,7 @@ __device__ __forceinline__ uint32_t vc_pack_quad(int s, int l, int td, const int
             }
         }
     }
-    if (SLOT_HITS && run_hits) atomicAdd(&stage[128 + run_slot], run_hits);
+    if (SLOT_HITS && run_hits) atomicAdd(&g_smem[stage + 128 + run_slot], run_hits);
     return hits;
 }
 
@@ -595,23 +613,23 @@ __device__ __forceinline__ Octet ld_octet(const int32_t* p) {
     return r;
 }
 template <bool SLOT_HITS, int HM, int SL>
-__device__ __forceinline__ uint32_t vc_pack_oct(int s, int l, int td, const int* sm,
-                                                const int32_t* __restrict__ dag_col, int m, int lane, int* stage,
+__device__ __forceinline__ uint32_t vc_pack_oct(int s, int l, int td,
+                                                const int32_t* __restrict__ dag_col, int m, int lane, int stage,
                                                 unsigned mult) {
     const unsigned nem = __ballot_sync(FULL, l > 0);
     if (nem == 0) return 0;
     const int c = __popc(nem);
     if (l > 0) {
         const int p = __popc(nem & lanemask_lt(lane));
-        stage[p] = s;
-        stage[32 + p] = s + l;
-        stage[64 + p] = td;
+        g_smem[stage + p] = s;
+        g_smem[stage + 32 + p] = s + l;
+        g_smem[stage + 64 + p] = td;
     }
     __syncwarp();
     const bool lst = lane < c;
-    const int cs = lst ? stage[lane] : 0;
-    const int ce = lst ? stage[32 + lane] : 0;
-    const int ctd = stage[64 + (lst ? lane : 0)];  // lanes past the lists alias list 0's table
+    const int cs = lst ? g_smem[stage + lane] : 0;
+    const int ce = lst ? g_smem[stage + 32 + lane] : 0;
+    const int ctd = g_smem[stage + 64 + (lst ? lane : 0)];  // lanes past the lists alias list 0's table
     __syncwarp();
     const int no = lst ? ((ce + 7) >> 3) - (cs >> 3) : 0;
     const int P = warp_incl_scan(no, lane);
@@ -620,7 +638,7 @@ __device__ __forceinline__ uint32_t vc_pack_oct(int s, int l, int td, const int*
     const int obias = (cs >> 3) - Pex;  // global octet index of combined octet f of this list: obias + f
     const unsigned le = lanemask_le(lane);
     uint32_t hits = 0;
-    unsigned* bm = reinterpret_cast<unsigned*>(stage + 160);
+    unsigned* bm = reinterpret_cast<unsigned*>(g_smem + stage + 160);
     const bool use_bm = total <= 32 * BITMAP_WORDS;
     if (use_bm) {
         bm[lane] = 0u;
@@ -667,21 +685,21 @@ __device__ __forceinline__ uint32_t vc_pack_oct(int s, int l, int td, const int*
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int h = bucket_of<HM>(k.v[j], lg, mult);
-            mb |= (unsigned)Bucket<SL>::at(sm, tab, h).match(k.v[j]) << j;
+            mb |= (unsigned)Bucket<SL>::at(tab, h).match(k.v[j]) << j;
         }
         const int hq = __popc(mb & slot_mask<8>(lo, hi));
         hits += hq;
         if (SLOT_HITS) {
             const int sl = (kd >> 21) & 31;
             if (sl != run_slot) {
-                if (run_hits) atomicAdd(&stage[128 + run_slot], run_hits);
+                if (run_hits) atomicAdd(&g_smem[stage + 128 + run_slot], run_hits);
                 run_slot = sl;
                 run_hits = 0;
             }
             run_hits += hq;
         }
     }
-    if (SLOT_HITS && run_hits) atomicAdd(&stage[128 + run_slot], run_hits);
+    if (SLOT_HITS && run_hits) atomicAdd(&g_smem[stage + 128 + run_slot], run_hits);
     return hits;
 }
 
@@ -692,8 +710,8 @@ __device__ __forceinline__ uint32_t vc_pack_oct(int s, int l, int td, const int*
 // and did not match walks the overflow chain. *done = quads processed.
 template <int HM, int SL, bool OVF, bool CHAIN>
 __device__ __forceinline__ uint32_t vc_range_quad(int s, int e, int nq, int tab, int lgB, int skip, int limit,
-                                                  const int* sm, const int32_t* __restrict__ dag_col, int m, int lane,
-                                                  int* stage, int* done, unsigned mult) {
+                                                  const int32_t* __restrict__ dag_col, int m, int lane,
+                                                  int stage, int* done, unsigned mult) {
     const unsigned nem = __ballot_sync(FULL, nq > 0);
     if (nem == 0) {
         *done = 0;
@@ -702,15 +720,15 @@ __device__ __forceinline__ uint32_t vc_range_quad(int s, int e, int nq, int tab,
     const int c = __popc(nem);
     if (nq > 0) {
         const int p = __popc(nem & lanemask_lt(lane));
-        stage[p] = s;
-        stage[32 + p] = e;
-        stage[64 + p] = nq;
+        g_smem[stage + p] = s;
+        g_smem[stage + 32 + p] = e;
+        g_smem[stage + 64 + p] = nq;
     }
     __syncwarp();
     const bool lst = lane < c;
-    const int cs = lst ? stage[lane] : 0;
-    const int ce = lst ? stage[32 + lane] : 0;
-    const int cq = lst ? stage[64 + lane] : 0;
+    const int cs = lst ? g_smem[stage + lane] : 0;
+    const int ce = lst ? g_smem[stage + 32 + lane] : 0;
+    const int cq = lst ? g_smem[stage + 64 + lane] : 0;
     __syncwarp();
     const int P = warp_incl_scan(cq, lane);
     const int total = __shfl_sync(FULL, P, 31);
@@ -757,16 +775,17 @@ __device__ __forceinline__ uint32_t vc_range_quad(int s, int e, int nq, int tab,
             for (int j = 0; j < 4; ++j) {
                 if (j >= lo[q] && j < hi[q]) {
                     const int h = bucket_of<HM>(key[j], lgB, mult);
-                    const Bucket<SL> b = Bucket<SL>::at(sm, tab, h);
+                    const Bucket<SL> b = Bucket<SL>::at(tab, h);
                     const int hit = bucket_match<SL, OVF>(b, key[j]);
                     hits += hit;
                     if (CHAIN) more |= (!hit && bucket_more<SL, OVF>(b)) << j;
                 }
             }
             if (CHAIN && __any_sync(FULL, more)) {
+#pragma unroll
                 for (int j = 0; j < 4; ++j)
                     if ((more >> j) & 1)
-                        hits += probe_chain<SL, OVF>(sm, tab, mask, bucket_of<HM>(key[j], lgB, mult), key[j]);
+                        hits += probe_next<SL, OVF>(tab, mask, bucket_of<HM>(key[j], lgB, mult), key[j]);
             }
         }
     }
@@ -781,8 +800,8 @@ __device__ __forceinline__ uint32_t vc_range_quad(int s, int e, int nq, int tab,
 // slots outside their list are masked. *done = octets processed.
 template <int HM, int SL, bool OVF, bool CHAIN>
 __device__ __forceinline__ uint32_t vc_range_oct(int s, int e, int no, int tab, int lgB, int skip, int limit,
-                                                 const int* sm, const int32_t* __restrict__ dag_col, int m, int lane,
-                                                 int* stage, int* done, unsigned mult) {
+                                                 const int32_t* __restrict__ dag_col, int m, int lane,
+                                                 int stage, int* done, unsigned mult) {
     const unsigned nem = __ballot_sync(FULL, no > 0);
     if (nem == 0) {
         *done = 0;
@@ -791,15 +810,15 @@ __device__ __forceinline__ uint32_t vc_range_oct(int s, int e, int no, int tab, 
     const int c = __popc(nem);
     if (no > 0) {
         const int p = __popc(nem & lanemask_lt(lane));
-        stage[p] = s;
-        stage[32 + p] = e;
-        stage[64 + p] = no;
+        g_smem[stage + p] = s;
+        g_smem[stage + 32 + p] = e;
+        g_smem[stage + 64 + p] = no;
     }
     __syncwarp();
     const bool lst = lane < c;
-    const int cs = lst ? stage[lane] : 0;
-    const int ce = lst ? stage[32 + lane] : 0;
-    const int co = lst ? stage[64 + lane] : 0;
+    const int cs = lst ? g_smem[stage + lane] : 0;
+    const int ce = lst ? g_smem[stage + 32 + lane] : 0;
+    const int co = lst ? g_smem[stage + 64 + lane] : 0;
     __syncwarp();
     const int P = warp_incl_scan(co, lane);
     const int total = __shfl_sync(FULL, P, 31);
@@ -832,20 +851,32 @@ __device__ __forceinline__ uint32_t vc_range_oct(int s, int e, int no, int tab, 
             }
         }
         int more = 0;  // bit j: slot j's bucket may have sent its key on and did not match
+        if constexpr (!CHAIN) {
+            // overflow-free table: every slot is probed and the mask keeps the list's
+            unsigned mb = 0;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if (j >= lo && j < hi) {
+            for (int j = 0; j < 8; ++j) {
                 const int h = bucket_of<HM>(k.v[j], lgB, mult);
-                const Bucket<SL> b = Bucket<SL>::at(sm, tab, h);
-                const int hit = bucket_match<SL, OVF>(b, k.v[j]);
-                hits += hit;
-                if (CHAIN) more |= (!hit && bucket_more<SL, OVF>(b)) << j;
+                mb |= (unsigned)bucket_match<SL, OVF>(Bucket<SL>::at(tab, h), k.v[j]) << j;
+            }
+            hits += __popc(mb & slot_mask<8>(lo, hi));
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (j >= lo && j < hi) {
+                    const int h = bucket_of<HM>(k.v[j], lgB, mult);
+                    const Bucket<SL> b = Bucket<SL>::at(tab, h);
+                    const int hit = bucket_match<SL, OVF>(b, k.v[j]);
+                    hits += hit;
+                    more |= (!hit && bucket_more<SL, OVF>(b)) << j;
+                }
             }
         }
         if (CHAIN && __any_sync(FULL, more)) {
+#pragma unroll
             for (int j = 0; j < 8; ++j)
                 if ((more >> j) & 1)
-                    hits += probe_chain<SL, OVF>(sm, tab, mask, bucket_of<HM>(k.v[j], lgB, mult), k.v[j]);
+                    hits += probe_next<SL, OVF>(tab, mask, bucket_of<HM>(k.v[j], lgB, mult), k.v[j]);
         }
     }
     *done = end > skip ? end - skip : 0;
@@ -863,22 +894,22 @@ __device__ __forceinline__ uint32_t vc_range_oct(int s, int e, int no, int tab, 
 // count is exact for packs built with or without chains.
 
 template <bool SLOT_HITS, int HM, int SL>
-__device__ __forceinline__ uint32_t probe_one(int key, int td, const int* sm, int* stage, unsigned mult) {
+__device__ __forceinline__ uint32_t probe_one(int key, int td, int stage, unsigned mult) {
     if (key < 0) return 0;
     const int lg = (td >> 16) & 31, tab = td & 0xffff;
     const int h = bucket_of<HM>(key, lg, mult);
-    const Bucket<SL> b = Bucket<SL>::at(sm, tab, h);
+    const Bucket<SL> b = Bucket<SL>::at(tab, h);
     int hit = b.match(key);
-    if (!hit && b.full()) hit = probe_chain<SL>(sm, tab, (1 << lg) - 1, h, key);
-    if (SLOT_HITS && hit) atomicAdd(&stage[128 + ((td >> 21) & 31)], 1);
+    if (!hit && b.full()) hit = probe_chain<SL>(tab, (1 << lg) - 1, h, key);
+    if (SLOT_HITS && hit) atomicAdd(&g_smem[stage + 128 + ((td >> 21) & 31)], 1);
     return (uint32_t)hit;
 }
 
 // Warp-centric: the whole warp walks one list at a time, lane j taking
 // entries j, j + 32, ...; lanes past the end of a short list idle.
 template <bool SLOT_HITS, int HM, int SL>
-__device__ __forceinline__ uint32_t balance_wc(int s, int l, int td, const int* sm,
-                                               const int32_t* __restrict__ dag_col, int lane, int* stage,
+__device__ __forceinline__ uint32_t balance_wc(int s, int l, int td,
+                                               const int32_t* __restrict__ dag_col, int lane, int stage,
                                                unsigned mult) {
     uint32_t hits = 0;
     unsigned lists = __ballot_sync(FULL, l > 0);
@@ -887,7 +918,7 @@ __device__ __forceinline__ uint32_t balance_wc(int s, int l, int td, const int* 
         lists &= lists - 1;
         const int sj = __shfl_sync(FULL, s, j), lj = __shfl_sync(FULL, l, j), tdj = __shfl_sync(FULL, td, j);
         for (int off = lane; off < lj; off += 32)
-            hits += probe_one<SLOT_HITS, HM, SL>(__ldg(dag_col + sj + off), tdj, sm, stage, mult);
+            hits += probe_one<SLOT_HITS, HM, SL>(__ldg(dag_col + sj + off), tdj, stage, mult);
     }
     return hits;
 }
@@ -896,8 +927,8 @@ __device__ __forceinline__ uint32_t balance_wc(int s, int l, int td, const int* 
 // one list per round, lane t of the subwarp taking entries t, t + S, ...; a
 // round lasts as long as its longest list.
 template <int S, bool SLOT_HITS, int HM, int SL>
-__device__ __forceinline__ uint32_t balance_sw(int s, int l, int td, const int* sm,
-                                               const int32_t* __restrict__ dag_col, int lane, int* stage,
+__device__ __forceinline__ uint32_t balance_sw(int s, int l, int td,
+                                               const int32_t* __restrict__ dag_col, int lane, int stage,
                                                unsigned mult) {
     constexpr int G = 32 / S;
     const int g = lane / S, t = lane % S;
@@ -910,7 +941,7 @@ __device__ __forceinline__ uint32_t balance_sw(int s, int l, int td, const int* 
         const int lmax = (int)__reduce_max_sync(FULL, (unsigned)lj);
         for (int off = t; off < lmax; off += S) {
             const int key = off < lj ? __ldg(dag_col + sj + off) : NOKEY;
-            hits += probe_one<SLOT_HITS, HM, SL>(key, tdj, sm, stage, mult);
+            hits += probe_one<SLOT_HITS, HM, SL>(key, tdj, stage, mult);
         }
     }
     return hits;
@@ -923,8 +954,8 @@ __device__ __forceinline__ uint32_t balance_sw(int s, int l, int td, const int* 
 // paper charges to this design.
 constexpr int PC_ROUND = 1024;
 template <bool SLOT_HITS, int HM, int SL>
-__device__ __forceinline__ uint32_t balance_pc(int s, int l, int td, const int* sm,
-                                               const int32_t* __restrict__ dag_col, int lane, int* stage,
+__device__ __forceinline__ uint32_t balance_pc(int s, int l, int td,
+                                               const int32_t* __restrict__ dag_col, int lane, int stage,
                                                unsigned mult, int2* buf) {
     const int P = warp_incl_scan(l, lane);
     const int total = __shfl_sync(FULL, P, 31);
@@ -944,7 +975,7 @@ __device__ __forceinline__ uint32_t balance_pc(int s, int l, int td, const int* 
         __syncwarp();
         for (int f = lane; f < r1 - r0; f += 32) {
             const int2 e = buf[f];
-            hits += probe_one<SLOT_HITS, HM, SL>(e.x, e.y, sm, stage, mult);
+            hits += probe_one<SLOT_HITS, HM, SL>(e.x, e.y, stage, mult);
         }
         __syncwarp();
     }
@@ -997,7 +1028,7 @@ __device__ __forceinline__ void list_bounds(int v, const int32_t* __restrict__ d
 }
 
 // Warp workers over packs of small vertices (2 <= d+ <= T_w).
-// smem per warp: area[area_ints] | stage[STAGE_INTS]. desc[i] = (first
+// smem per warp: area[area_ints] | g_smem[stage + STAGE_INTS]. desc[i] = (first
 // out-edge, d+) of warp_list[i]. A pack's area holds all its tables' slots
 // first, then all their length words.
 // BAL: TC_BALANCE_VC (the design) or one of the Sec. 4.2 alternatives above;
@@ -1014,7 +1045,6 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
                  unsigned long long* __restrict__ per_vertex, DevCounters* ctr, int n, int area_ints,
                  int lg_min_buckets, int pop, int quad, int timing, const int2* __restrict__ dag_bnd,
                  int2* __restrict__ pc_buf, int strided) {
-    extern __shared__ int smem[];
     if (ctr->err) return;
     if (quad == 2 && (100LL * ctr->n_block >= (long long)ctr->n_warp) != OCT) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1022,7 +1052,7 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
     long long cyc_b = 0, cyc_p = 0;               // build / probe cycles (timing only)
     const unsigned le = lanemask_le(lane);
     const int area = w * (area_ints + STAGE_INTS);  // int offset of this warp's area in smem
-    int* stage = smem + area + area_ints;
+    const int stage = area + area_ints;  // int offset of this warp's stage
     const int nlist = ctr->n_warp;
     unsigned long long acc = 0;
     // A pop takes up to `pop` vertices of the warp list, fewer when the list
@@ -1065,7 +1095,7 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
             const int tab_used = __shfl_sync(FULL, FT, p1 - 1), len_used = __shfl_sync(FULL, FL, p1 - 1);
             const int my_tab = area + FT - ft;                  // slots of this lane's table
             const int my_len = area + tab_used + FL - fl;       // its length words
-            if (PER_VERTEX) stage[128 + lane] = 0;
+            if (PER_VERTEX) g_smem[stage + 128 + lane] = 0;
             // build every table of the pack from the pack's out-lists, one flat
             // array; if any key misses its home bucket, rebuild the pack with the
             // next hash multiplier (up to 4), else probe with overflow chains
@@ -1079,9 +1109,9 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
             bool chained = false;
             for (int attempt = 0;; ++attempt) {
                 for (int t = lane * 4; t < tab_used; t += 128)
-                    *reinterpret_cast<int4*>(smem + area + t) = make_int4(EMPTY, EMPTY, EMPTY, EMPTY);
+                    *reinterpret_cast<int4*>(g_smem + area + t) = make_int4(EMPTY, EMPTY, EMPTY, EMPTY);
                 for (int t = lane * 4; t < len_used; t += 128)
-                    *reinterpret_cast<int4*>(smem + area + tab_used + t) = make_int4(0, 0, 0, 0);
+                    *reinterpret_cast<int4*>(g_smem + area + tab_used + t) = make_int4(0, 0, 0, 0);
                 __syncwarp();
                 int ovf = 0;
                 for (int b0 = 0; b0 < E; b0 += 32 * VC_UNROLL) {
@@ -1099,7 +1129,7 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
                         const int tb = __shfl_sync(FULL, my_tab, own[q]);
                         const int lw = __shfl_sync(FULL, my_len, own[q]);
                         const int lg = __shfl_sync(FULL, lgB, own[q]);
-                        if (key[q] >= 0) ovf |= insert_b4<HM, PACK_SLOTS>(smem, tb, lw, lg, key[q], mult);
+                        if (key[q] >= 0) ovf |= insert_b4<HM, PACK_SLOTS>(tb, lw, lg, key[q], mult);
                     }
                 }
                 __syncwarp();
@@ -1137,31 +1167,31 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
                 if (BAL != TC_BALANCE_VC) {
                     const int td = etab | (elg << 16) | (eslot << 21);
                     if (BAL == TC_BALANCE_WC)
-                        hits += balance_wc<PER_VERTEX, HM, PACK_SLOTS>(s, l, td, smem, dag_col, lane, stage, mult);
+                        hits += balance_wc<PER_VERTEX, HM, PACK_SLOTS>(s, l, td, dag_col, lane, stage, mult);
                     else if (BAL == TC_BALANCE_SW8)
-                        hits += balance_sw<8, PER_VERTEX, HM, PACK_SLOTS>(s, l, td, smem, dag_col, lane, stage, mult);
+                        hits += balance_sw<8, PER_VERTEX, HM, PACK_SLOTS>(s, l, td, dag_col, lane, stage, mult);
                     else if (BAL == TC_BALANCE_SW16)
-                        hits += balance_sw<16, PER_VERTEX, HM, PACK_SLOTS>(s, l, td, smem, dag_col, lane, stage, mult);
+                        hits += balance_sw<16, PER_VERTEX, HM, PACK_SLOTS>(s, l, td, dag_col, lane, stage, mult);
                     else
                         hits += balance_pc<PER_VERTEX, HM, PACK_SLOTS>(
-                            s, l, td, smem, dag_col, lane, stage, mult,
+                            s, l, td, dag_col, lane, stage, mult,
                             pc_buf + ((size_t)blockIdx.x * (blockDim.x >> 5) + w) * PC_ROUND);
                 } else if (OCT && !chained && quad == 2 &&
                            __reduce_add_sync(FULL, (unsigned)l) >=
                                (unsigned)OCT_MIN_AVG * __popc(__ballot_sync(FULL, l > 0))) {
                     // octets pay off on long 2-hop lists; on short ones their alignment
                     // and tail slots cost more than the saved owner work (quads below)
-                    hits += vc_pack_oct<PER_VERTEX, HM, PACK_SLOTS>(s, l, etab | (elg << 16) | (eslot << 21), smem,
+                    hits += vc_pack_oct<PER_VERTEX, HM, PACK_SLOTS>(s, l, etab | (elg << 16) | (eslot << 21),
                                                                     dag_col, m, lane, stage, mult);
                 } else if (!chained && quad) {
-                    hits += vc_pack_quad<PER_VERTEX, HM, PACK_SLOTS>(s, l, etab | (elg << 16) | (eslot << 21), smem, dag_col,
+                    hits += vc_pack_quad<PER_VERTEX, HM, PACK_SLOTS>(s, l, etab | (elg << 16) | (eslot << 21), dag_col,
                                                          m, lane, stage, mult);
                 } else if (!chained) {
-                    hits += vc_pack_fast<PER_VERTEX, HM, PACK_SLOTS>(s, l, etab | (elg << 16) | (eslot << 21), smem, dag_col,
+                    hits += vc_pack_fast<PER_VERTEX, HM, PACK_SLOTS>(s, l, etab | (elg << 16) | (eslot << 21), dag_col,
                                                          lane, stage, mult);
                 } else {
                     int done;
-                    hits += vc_range_b4<PER_VERTEX, HM, PACK_SLOTS>(s, l, etab, elg, eslot, 0, 0x7fffffff, smem, dag_col, lane,
+                    hits += vc_range_b4<PER_VERTEX, HM, PACK_SLOTS>(s, l, etab, elg, eslot, 0, 0x7fffffff, dag_col, lane,
                                                         stage, &done, mult);
                 }
                 s = ns;
@@ -1174,7 +1204,7 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
             if (timing) cyc_p += clock64() - t_probe;
             if (PER_VERTEX) {
                 __syncwarp();
-                if (in) per_vertex[__ldg(warp_list + li)] = (unsigned long long)stage[128 + lane];
+                if (in) per_vertex[__ldg(warp_list + li)] = (unsigned long long)g_smem[stage + 128 + lane];
             }
             __syncwarp();
             p0 = p1;
@@ -1189,7 +1219,7 @@ __global__ void __launch_bounds__(256, PACK_MIN_BLOCKS)
 
 // Thread-block workers: one block per work item (u, out-neighbours
 // [nb0, nb1)) of a vertex with d+ > T_w; nb1 - nb0 <= item_nbrs <= 1024.
-// smem: stage[nwarps * BLOCK_STAGE_INTS] | S[item_nbrs] | LP[item_nbrs] | table.
+// smem: g_smem[stage + nwarps * BLOCK_STAGE_INTS] | S[item_nbrs] | LP[item_nbrs] | table.
 // The block loads the item's out-neighbours' list bounds (S = starts, LP =
 // inclusive prefix of lengths) once, builds the table of one part of N+(u),
 // and its warps take pieces of PIECE combined 2-hop indices from a shared
@@ -1202,15 +1232,14 @@ __global__ void __launch_bounds__(1024, 1)
                   const int2* __restrict__ items, unsigned long long* __restrict__ per_vertex, DevCounters* ctr,
                   int n, int table_off, int part_max, int item_nbrs, int quad, int timing,
                   const int2* __restrict__ dag_bnd) {
-    extern __shared__ int smem[];
     __shared__ int s_item, s_piece;
     __shared__ int s_wsum[32];
     if (ctr->err) return;
     long long cyc_b = 0, cyc_p = 0;  // build / probe cycles of this warp (timing only)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int m = quad ? (dag_bnd ? dag_bnd[n].x : __ldg(dag_ptr + n)) : 0;  // readable dag_col entries
-    int* stage = smem + w * BLOCK_STAGE_INTS;
-    int* S = smem + nw * BLOCK_STAGE_INTS;
+    const int stage = w * BLOCK_STAGE_INTS;  // int offset of this warp's stage
+    int* S = g_smem + nw * BLOCK_STAGE_INTS;
     int* E = S + item_nbrs;
     int* LP = E + item_nbrs;
     const int nitems = ctr->n_items;
@@ -1259,10 +1288,10 @@ __global__ void __launch_bounds__(1024, 1)
             const int B = next_pow2(pk < 32 ? 32 : pk) << BLOCK_SPARSE;
             const int lgB = 31 - __clz(B) + (BLOCK_SLOTS == 2 ? 1 : 0);  // log2 of the bucket count
             const long long t_build = timing ? clock64() : 0;
-            int* tab = smem + table_off;
+            int* tab = g_smem + table_off;
             const int lenw = table_off + 4 * B;
             // build; if a key missed its home bucket, rebuild with the next hash
-            // multiplier (BLOCK_REHASH, up to 4 tries) so that every key sits in its
+            // multiplier (up to BLOCK_REHASH times) so that every key sits in its
             // home bucket and probes need no overflow chain; a table that still
             // overflows is probed with chains (its overflowed buckets marked)
             unsigned mult = kHashMult0;
@@ -1270,17 +1299,17 @@ __global__ void __launch_bounds__(1024, 1)
             for (int attempt = 0;; ++attempt) {
                 for (int t = threadIdx.x * 4; t < 4 * B; t += blockDim.x * 4)
                     *reinterpret_cast<int4*>(tab + t) = make_int4(EMPTY, EMPTY, EMPTY, EMPTY);
-                for (int t = threadIdx.x; t < B; t += blockDim.x) smem[lenw + t] = 0;
+                for (int t = threadIdx.x; t < B; t += blockDim.x) g_smem[lenw + t] = 0;
                 if (threadIdx.x == 0) s_piece = 0;
                 __syncthreads();
                 int ovf = 0;
                 for (int t = threadIdx.x; t < pk; t += blockDim.x)
-                    ovf |= insert_b4w<HM, BLOCK_SLOTS>(smem, table_off, lenw, lgB, __ldg(dag_col + a + p0 + t), mult);
+                    ovf |= insert_b4w<HM, BLOCK_SLOTS>(table_off, lenw, lgB, __ldg(dag_col + a + p0 + t), mult);
                 if (!__syncthreads_or(ovf)) break;
-                if (!BLOCK_REHASH || HM == 1 || attempt == 3) {
+                if (HM == 1 || attempt >= BLOCK_REHASH) {
                     chained = true;
                     if (BLOCK_OVF) {
-                        mark_overflow<BLOCK_SLOTS>(smem, table_off, lenw, 1 << lgB);
+                        mark_overflow<BLOCK_SLOTS>(table_off, lenw, 1 << lgB);
                         __syncthreads();
                     }
                     break;
@@ -1316,25 +1345,25 @@ __global__ void __launch_bounds__(1024, 1)
                         const int ej = j < cnt ? E[j] : 0;
                         if (!chained)
                             h += vc_range_oct<HM, BLOCK_SLOTS, false, false>(sj, ej, uj, table_off, lgB,
-                                                                             F - base_flat, F1 - base_flat, smem,
+                                                                             F - base_flat, F1 - base_flat,
                                                                              dag_col, m, lane, stage, &done, mult);
                         else
                             h += vc_range_oct<HM, BLOCK_SLOTS, BLOCK_OVF, true>(sj, ej, uj, table_off, lgB,
-                                                                                F - base_flat, F1 - base_flat, smem,
+                                                                                F - base_flat, F1 - base_flat,
                                                                                 dag_col, m, lane, stage, &done, mult);
                     } else if (quad && !chained) {
                         const int ej = j < cnt ? E[j] : 0;
                         h += vc_range_quad<HM, BLOCK_SLOTS, false, false>(sj, ej, uj, table_off, lgB, F - base_flat,
-                                                                          F1 - base_flat, smem, dag_col, m, lane,
+                                                                          F1 - base_flat, dag_col, m, lane,
                                                                           stage, &done, mult);
                     } else if (quad) {
                         const int ej = j < cnt ? E[j] : 0;
                         h += vc_range_quad<HM, BLOCK_SLOTS, BLOCK_OVF, true>(sj, ej, uj, table_off, lgB,
-                                                                             F - base_flat, F1 - base_flat, smem,
+                                                                             F - base_flat, F1 - base_flat,
                                                                              dag_col, m, lane, stage, &done, mult);
                     } else {
                         h += vc_range_b4<false, HM, BLOCK_SLOTS, BLOCK_OVF>(sj, uj, table_off, lgB, 0, F - base_flat,
-                                                                            F1 - base_flat, smem, dag_col, lane,
+                                                                            F1 - base_flat, dag_col, lane,
                                                                             stage, &done, mult);
                     }
                     F += done;
@@ -1368,7 +1397,6 @@ __global__ void __launch_bounds__(256) k_count_edge(const int32_t* __restrict__ 
                                                    unsigned long long* __restrict__ per_vertex, DevCounters* ctr,
                                                    int n, int area_ints, int part_max, int shard_count,
                                                    int shard_index, int timing) {
-    extern __shared__ int smem[];
     if (ctr->err) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int area = w * (area_ints + STAGE_INTS);
@@ -1394,19 +1422,19 @@ __global__ void __launch_bounds__(256) k_count_edge(const int32_t* __restrict__ 
                 const int B = 1 << lgB;
                 const int tab = area, lenw = area + 4 * B;
                 for (int t = lane * 4; t < 4 * B; t += 128)
-                    *reinterpret_cast<int4*>(smem + tab + t) = make_int4(EMPTY, EMPTY, EMPTY, EMPTY);
-                for (int t = lane; t < B / 4; t += 32) smem[lenw + t] = 0;
+                    *reinterpret_cast<int4*>(g_smem + tab + t) = make_int4(EMPTY, EMPTY, EMPTY, EMPTY);
+                for (int t = lane; t < B / 4; t += 32) g_smem[lenw + t] = 0;
                 __syncwarp();
-                for (int t = lane; t < pk; t += 32) insert_b4<HM>(smem, tab, lenw, lgB, __ldg(dag_col + a + p0 + t),
+                for (int t = lane; t < pk; t += 32) insert_b4<HM>(tab, lenw, lgB, __ldg(dag_col + a + p0 + t),
                                                                  kHashMult0);
                 __syncwarp();
                 const long long t1 = timing ? clock64() : 0;
                 for (int i = lane; i < l; i += 32) {
                     const int key = __ldg(dag_col + s + i);
                     const int h = bucket_of<HM>(key, lgB);
-                    const int4 b4 = *reinterpret_cast<const int4*>(smem + tab + 4 * h);
+                    const int4 b4 = *reinterpret_cast<const int4*>(g_smem + tab + 4 * h);
                     int hit = match4(b4, key);
-                    if (!hit && b4.w != EMPTY) hit = probe_chain<4>(smem, tab, B - 1, h, key);
+                    if (!hit && b4.w != EMPTY) hit = probe_chain<4>(tab, B - 1, h, key);
                     hu += hit;
                 }
                 __syncwarp();
