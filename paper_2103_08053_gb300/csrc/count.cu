@@ -48,14 +48,18 @@
 // not all fit their home buckets is rebuilt with another hash multiplier, so
 // its probes need no overflow chain (k_count_pack).
 //
-// Thread-block tables use 4-slot (16-byte) buckets, B = nextpow2(part)
-// buckets (at most one key per bucket on average) and one 32-bit length word
+// Thread-block tables use 4-slot (16-byte) buckets, B = 2 * nextpow2(part)
+// buckets where that fits the block's budget, else the largest B that fits
+// (at most one key per bucket on average), and one 32-bit length word
 // per bucket (a bucket of a large table can see more than 255 claims), where
 // N+(u) is split into parts of at most P_max keys (the largest power of two
 // whose table fits the block's shared memory), each probed by the whole
-// 2-hop list: |N+(u) ∩ N+(v)| = sum over parts of |part ∩ N+(v)|. After a
-// build, buckets that received more claims than slots are marked
-// (mark_overflow); only a marked bucket sends a search on to the next one.
+// 2-hop list: |N+(u) ∩ N+(v)| = sum over parts of |part ∩ N+(v)|. A table in
+// which a key missed its home bucket is rebuilt with the next hash multiplier
+// (up to BLOCK_REHASH times); probes of an overflow-free table need no chain
+// checks. In a table that still overflows, buckets that received more claims
+// than slots are marked (mark_overflow), and only a marked bucket sends a
+// search on to the next one.
 #include <mutex>
 
 #include "tc_internal.h"
@@ -98,8 +102,8 @@ static_assert(VC_UNROLL == 4, "the bitmap owner path reads four window words at 
 #ifndef BLOCK_REHASH
 #define BLOCK_REHASH 3  // rebuilds of a thread-block table with a displaced key, each with the next hash multiplier (0..3)
 #endif
-#ifndef BLOCK_SPARSE
-#define BLOCK_SPARSE 0  // log2 of the extra bucket factor of thread-block tables (B = nextpow2(part) << this)
+#ifndef BLOCK_SPREAD
+#define BLOCK_SPREAD 2  // thread-block tables: B = BLOCK_SPREAD * nextpow2(part) buckets when that fits the budget
 #endif
 
 // Dynamic shared memory of the counting kernels. The device helpers index
@@ -1282,10 +1286,12 @@ __global__ void __launch_bounds__(1024, 1)
         uint32_t h = 0;
         for (int p0 = 0; p0 < k && W > 0; p0 += part_max) {
             const int pk = min(part_max, k - p0);
-            // 4 * nextpow2(part) slots in buckets of BLOCK_SLOTS, then one
-            // length word per 4 slots (32-bit lengths for 4-slot buckets,
-            // two 16-bit lengths for 2-slot buckets)
-            const int B = next_pow2(pk < 32 ? 32 : pk) << BLOCK_SPARSE;
+            // 4B slots in buckets of BLOCK_SLOTS, then one length word per 4 slots
+            // (32-bit lengths for 4-slot buckets, two 16-bit lengths for 2-slot
+            // buckets); at most 1/2 key per 4-slot bucket where the budget allows (such a table is
+            // almost always overflow-free after at most one rebuild); the largest
+            // parts get the largest table that fits (part_max buckets, up to one key each)
+            const int B = min(BLOCK_SPREAD * next_pow2(pk < 32 ? 32 : pk), part_max);
             const int lgB = 31 - __clz(B) + (BLOCK_SLOTS == 2 ? 1 : 0);  // log2 of the bucket count
             const long long t_build = timing ? clock64() : 0;
             int* tab = g_smem + table_off;
@@ -1631,12 +1637,12 @@ int count_block_budget_ints(const CountCfg& cfg) {
     return cfg.block_smem_bytes / 4 - (cfg.block_threads / 32) * BLOCK_STAGE_INTS - 3 * cfg.item_neighbors;
 }
 
-// Largest part of N+(u) whose thread-block table (B = nextpow2(part) << BLOCK_SPARSE,
-// 4B slots + B length words) fits the budget.
+// Largest part of N+(u) whose thread-block table of B = nextpow2(part) buckets
+// (4B slots + B length words) fits the budget; also the most buckets a table has.
 int count_block_part_max(const CountCfg& cfg) {
     const int budget = count_block_budget_ints(cfg);
     int p = 32;
-    while ((5 * (2 * p) << BLOCK_SPARSE) <= budget) p *= 2;
+    while (5 * (2 * p) <= budget) p *= 2;
     return p;
 }
 
