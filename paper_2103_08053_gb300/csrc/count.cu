@@ -102,6 +102,9 @@ static_assert(VC_UNROLL == 4, "the bitmap owner path reads four window words at 
 #ifndef BLOCK_REHASH
 #define BLOCK_REHASH 3  // rebuilds of a thread-block table with a displaced key, each with the next hash multiplier (0..3)
 #endif
+#ifndef BLOCK_FILTER
+#define BLOCK_FILTER 1  // 1: overflow-free thread-block tables keep a 32-bit key signature per bucket, probed first
+#endif
 #ifndef BLOCK_SPREAD
 #define BLOCK_SPREAD 2  // thread-block tables: B = BLOCK_SPREAD * nextpow2(part) buckets when that fits the budget
 #endif
@@ -181,6 +184,16 @@ template <int HM>
 __device__ __forceinline__ int bucket_of(int w, int lgB, unsigned mult = kHashMult0) {
     if (HM == 1) return w & ((1 << lgB) - 1);
     return (int)(((unsigned)w * mult) >> (32 - lgB));
+}
+
+// Signature bit of key w in a table of 2^lgB buckets (lgB <= 27): the five
+// hash bits below the bucket bits (multiplicative hash), or the five id bits
+// above them (x mod B). A bucket's signature word has the bits of its keys, so
+// a key whose bit is clear in its home bucket's word is not in the bucket.
+template <int HM>
+__device__ __forceinline__ int sig_bit(int w, int lgB, unsigned mult) {
+    if (HM == 1) return (int)(((unsigned)w >> lgB) & 31u);
+    return (int)((((unsigned)w * mult) >> (27 - lgB)) & 31u);
 }
 
 // ---- table builds (bucket-major buckets of SL slots) ------------------------
@@ -802,10 +815,10 @@ __device__ __forceinline__ uint32_t vc_range_quad(int s, int e, int nq, int tab,
 // groups of eight entries); the combined octet indices [skip, min(limit,
 // total)) are dealt one per lane per step, each read with one 256-bit load;
 // slots outside their list are masked. *done = octets processed.
-template <int HM, int SL, bool OVF, bool CHAIN>
+template <int HM, int SL, bool OVF, bool CHAIN, bool FILT = false>
 __device__ __forceinline__ uint32_t vc_range_oct(int s, int e, int no, int tab, int lgB, int skip, int limit,
                                                  const int32_t* __restrict__ dag_col, int m, int lane,
-                                                 int stage, int* done, unsigned mult) {
+                                                 int stage, int* done, unsigned mult, int sig = 0) {
     const unsigned nem = __ballot_sync(FULL, no > 0);
     if (nem == 0) {
         *done = 0;
@@ -855,7 +868,23 @@ __device__ __forceinline__ uint32_t vc_range_oct(int s, int e, int no, int tab, 
             }
         }
         int more = 0;  // bit j: slot j's bucket may have sent its key on and did not match
-        if constexpr (!CHAIN) {
+        if constexpr (!CHAIN && FILT) {
+            // overflow-free table with bucket signatures (int offset sig): every
+            // slot's signature word is read (4 bytes), and only the list's slots
+            // whose bit is set load their bucket (16 bytes)
+            int hb[8];
+            unsigned pass = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                hb[j] = bucket_of<HM>(k.v[j], lgB, mult);
+                const unsigned sw = (unsigned)g_smem[sig + hb[j]];
+                pass |= ((sw >> sig_bit<HM>(k.v[j], lgB, mult)) & 1u) << j;
+            }
+            pass &= slot_mask<8>(lo, hi);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (pass & (1u << j)) hits += Bucket<SL>::at(tab, hb[j]).match(k.v[j]);
+        } else if constexpr (!CHAIN) {
             // overflow-free table: every slot is probed and the mask keeps the list's
             unsigned mb = 0;
 #pragma unroll
@@ -1322,6 +1351,21 @@ __global__ void __launch_bounds__(1024, 1)
                 }
                 mult = hash_mult(attempt + 1);
             }
+            constexpr bool kFilter = BLOCK_FILTER && BLOCK_SLOTS == 4;
+            if (kFilter && !chained) {
+                // overflow-free: every key sits in its home bucket; the bucket's length
+                // word (no longer needed) becomes its signature
+                for (int t = threadIdx.x; t < B; t += blockDim.x) {
+                    const int4 q = *reinterpret_cast<const int4*>(tab + 4 * t);
+                    unsigned sg = 0;
+                    if (q.x != EMPTY) sg |= 1u << sig_bit<HM>(q.x, lgB, mult);
+                    if (q.y != EMPTY) sg |= 1u << sig_bit<HM>(q.y, lgB, mult);
+                    if (q.z != EMPTY) sg |= 1u << sig_bit<HM>(q.z, lgB, mult);
+                    if (q.w != EMPTY) sg |= 1u << sig_bit<HM>(q.w, lgB, mult);
+                    g_smem[lenw + t] = (int)sg;
+                }
+                __syncthreads();
+            }
             const long long t_probe = timing ? clock64() : 0;
             if (timing) cyc_b += t_probe - t_build;
             // combined units (quads or keys) per piece: about 2 pieces per warp
@@ -1350,9 +1394,9 @@ __global__ void __launch_bounds__(1024, 1)
                     if (quad == 2) {
                         const int ej = j < cnt ? E[j] : 0;
                         if (!chained)
-                            h += vc_range_oct<HM, BLOCK_SLOTS, false, false>(sj, ej, uj, table_off, lgB,
-                                                                             F - base_flat, F1 - base_flat,
-                                                                             dag_col, m, lane, stage, &done, mult);
+                            h += vc_range_oct<HM, BLOCK_SLOTS, false, false, kFilter>(
+                                sj, ej, uj, table_off, lgB, F - base_flat, F1 - base_flat, dag_col, m, lane, stage,
+                                &done, mult, lenw);
                         else
                             h += vc_range_oct<HM, BLOCK_SLOTS, BLOCK_OVF, true>(sj, ej, uj, table_off, lgB,
                                                                                 F - base_flat, F1 - base_flat,
