@@ -456,13 +456,54 @@ def reorder_profile_run(args):
 # -------------------------------------------------------------- the arms
 
 def pinned_copy(torch, a):
-    """A page-locked host copy of numpy array `a`. (Allocated page-locked and
-    then filled: on the GB300 machine, tensor.pin_memory() copies of multi-GB
-    arrays were read by the copy engine at 63 GB/s, buffers allocated
-    page-locked at 210 GB/s.)"""
+    """A page-locked host copy of numpy array `a` (allocated page-locked,
+    then filled)."""
     t = torch.empty(a.shape, dtype=torch.from_numpy(a[:0]).dtype, pin_memory=True)
     t.copy_(torch.from_numpy(a))
     return t
+
+
+class HugePinned:
+    """A page-locked host copy of a large numpy array in 2 MiB pages: anonymous
+    memory mapped with madvise(MADV_HUGEPAGE), filled, then registered with
+    cudaHostRegister. On the GB300 machine the copy engine read such buffers at
+    209-211 GB/s, while multi-GB buffers from the page-locked allocator, made
+    after the graph generation had churned host memory, were read at 50-210
+    GB/s from one process to the next. `array` is the host view; close()
+    unregisters and unmaps."""
+
+    def __init__(self, torch, a):
+        import ctypes
+
+        import numpy as np
+        self._libc = ctypes.CDLL("libc.so.6", use_errno=True)
+        self._libc.mmap.restype = ctypes.c_void_p
+        self._libc.mmap.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_long]
+        self._libc.madvise.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+        self._libc.munmap.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
+        self._cudart = torch.cuda.cudart()
+        self.nbytes = max((a.nbytes + (2 << 20) - 1) // (2 << 20) * (2 << 20), 2 << 20)
+        p = self._libc.mmap(None, self.nbytes, 3, 0x22, -1, 0)  # PROT_READ|PROT_WRITE, MAP_PRIVATE|MAP_ANONYMOUS
+        if p in (None, ctypes.c_void_p(-1).value):
+            raise MemoryError("mmap failed")
+        self.ptr = p
+        self._libc.madvise(p, self.nbytes, 14)  # MADV_HUGEPAGE (advice only; 4 KiB pages still work)
+        buf = (ctypes.c_char * self.nbytes).from_address(p)
+        self.array = np.frombuffer(buf, dtype=a.dtype, count=a.size)
+        self.array[:] = a.reshape(-1)
+        err = self._cudart.cudaHostRegister(p, self.nbytes, 0)
+        self.registered = int(err) == 0 if not hasattr(err, "value") else err.value == 0
+        if not self.registered:
+            raise RuntimeError(f"cudaHostRegister failed: {err}")
+
+    def close(self):
+        if self.ptr:
+            if self.registered:
+                self._cudart.cudaHostUnregister(self.ptr)
+            self.array = None
+            self._libc.munmap(self.ptr, self.nbytes)
+            self.ptr = None
 
 
 def measure_graph(T, torch, dev, key, spec, g, steps, warmup, rank, world, dist, e2e_steps, clocks):
@@ -525,8 +566,8 @@ def measure_graph(T, torch, dev, key, spec, g, steps, warmup, rank, world, dist,
 
     # end to end through the C ABI from pinned host memory: H2D of the CSR, the
     # whole path, D2H of the count, every step
-    rp_pin = pinned_copy(torch, rp_h)
-    col_pin = pinned_copy(torch, col_h)
+    rp_hp, col_hp = HugePinned(torch, rp_h), HugePinned(torch, col_h)
+    rp_pin, col_pin = torch.from_numpy(rp_hp.array), torch.from_numpy(col_hp.array)
     for _ in range(3):
         ctx.count_host(g.n, rp_pin.numpy(), col_pin.numpy(), stream=stream)
     torch.cuda.synchronize(dev)
@@ -557,6 +598,8 @@ def measure_graph(T, torch, dev, key, spec, g, steps, warmup, rank, world, dist,
     torch.cuda.synchronize(dev)
     h2d_ms = h0.elapsed_time(h1) / 3
     del rp_d, col_d, rp_pin, col_pin
+    rp_hp.close()
+    col_hp.close()
     ctx.read_timing()
     ctx.close()
 
@@ -588,7 +631,7 @@ def measure_graph(T, torch, dev, key, spec, g, steps, warmup, rank, world, dist,
                 "stat": f"median of {e2e_steps} timed calls", "mean_ms_per_step": e2e_mean_ms,
                 "max_ms_per_step": max(e2e_each),
                 "h2d_bytes_per_step": int(rp_h.nbytes + col_h.nbytes), "d2h_bytes_per_step": 16,
-                "h2d_copy_ms": h2d_ms, "host_pinned": True,
+                "h2d_copy_ms": h2d_ms, "host_pinned": "cudaHostRegister of 2 MiB-page (madvise) host buffers",
                 "count_equal_device": e2e_count == my_count,
                 "api": "tc_count_host (pinned host CSR)"},
         "gpu_launches": launches,
