@@ -215,6 +215,44 @@ def test_octet_and_quad_builds_per_vertex(T, skewed):
         assert c.count(g.n, rp, col) == want_total
 
 
+def hub_spoke_graph(hubs=300, spokes=6000, per_spoke=8, seed=46):
+    """A clique of `hubs` vertices and `spokes` small vertices, each joined to
+    `per_spoke` random hubs. After orientation a spoke points at hubs (their
+    degree is higher), whose out-lists within the clique average about
+    hubs / 2 keys, and the hubs with d+ > 128 are thread-block vertices."""
+    rng = np.random.default_rng(seed)
+    i, j = np.triu_indices(hubs, 1)
+    src = [i, np.repeat(np.arange(hubs, hubs + spokes), per_spoke)]
+    dst = [j, np.concatenate([rng.choice(hubs, per_spoke, replace=False) for _ in range(spokes)])]
+    return G.csr_from_edges(hubs + spokes, np.concatenate(src).astype(np.int32), np.concatenate(dst).astype(np.int32))
+
+
+def test_octet_path_of_the_warp_workers(T):
+    # the warp workers' 32-byte octet loads run only in the octet build and only
+    # for chunks whose 2-hop lists average at least 64 keys: here every spoke's
+    # out-edges point at hubs with out-lists of about 150 keys, and about 170 of
+    # the 6300 counted vertices are thread-block vertices (>= 1 %: the octet
+    # build works); per-vertex counts against the oracle
+    g = hub_spoke_graph()
+    od = oracle.orient(g)
+    spokes = np.arange(300, g.n)
+    dplus = od.out_degrees()
+    assert (dplus[spokes] == 8).all()
+    lens = dplus[od.dag_col[od.dag_ptr[300]:]]
+    assert lens.mean() >= 64
+    want_total, want_pv = oracle.count_dag(od, per_vertex=True)
+    with T.Context(0) as c:
+        rp, col = dev(g)
+        d = c.orient(g.n, rp, col)
+        st = c.dag_stats(d)
+        assert 100 * st["n_block"] >= st["n_warp"] and st["n_warp"] >= 6000
+        pv = torch.zeros(g.n, dtype=torch.int64, device="cuda")
+        assert c.count_dag(d, per_vertex=pv) == want_total
+        assert np.array_equal(pv.cpu().numpy().astype(np.uint64), want_pv)
+        d.free()
+        assert c.count(g.n, rp, col) == want_total
+
+
 def test_unaligned_dag_and_ragged_quads(ctx):
     # wide loads need an aligned dag_col: 32-byte octets at shift 0, 16-byte
     # quads at shift 4 (16 bytes), one key per lane otherwise. All must equal
