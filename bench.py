@@ -497,6 +497,22 @@ class HugePinned:
         if not self.registered:
             raise RuntimeError(f"cudaHostRegister failed: {err}")
 
+    def hugepage_fraction(self) -> float:
+        """Share of the buffer in transparent huge pages (/proc/self/smaps)."""
+        import re
+        huge, cur = 0, False
+        try:
+            for line in open("/proc/self/smaps"):
+                m = re.match(r"([0-9a-f]+)-([0-9a-f]+) ", line)
+                if m:
+                    a, b = int(m.group(1), 16), int(m.group(2), 16)
+                    cur = a < self.ptr + self.nbytes and self.ptr < b
+                elif cur and line.startswith("AnonHugePages:"):
+                    huge += int(line.split()[1]) * 1024
+        except OSError:
+            return -1.0
+        return huge / self.nbytes
+
     def close(self):
         if self.ptr:
             if self.registered:
@@ -597,6 +613,7 @@ def measure_graph(T, torch, dev, key, spec, g, steps, warmup, rank, world, dist,
     h1.record(stream)
     torch.cuda.synchronize(dev)
     h2d_ms = h0.elapsed_time(h1) / 3
+    huge = col_hp.hugepage_fraction()
     del rp_d, col_d, rp_pin, col_pin
     rp_hp.close()
     col_hp.close()
@@ -632,6 +649,7 @@ def measure_graph(T, torch, dev, key, spec, g, steps, warmup, rank, world, dist,
                 "max_ms_per_step": max(e2e_each),
                 "h2d_bytes_per_step": int(rp_h.nbytes + col_h.nbytes), "d2h_bytes_per_step": 16,
                 "h2d_copy_ms": h2d_ms, "host_pinned": "cudaHostRegister of 2 MiB-page (madvise) host buffers",
+                "host_hugepage_fraction": round(huge, 3),
                 "count_equal_device": e2e_count == my_count,
                 "api": "tc_count_host (pinned host CSR)"},
         "gpu_launches": launches,

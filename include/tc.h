@@ -136,7 +136,11 @@ typedef struct {
                                     smallest id of the closed neighbourhood {u} + N(u), a min-hash of
                                     N(u) -- so that vertices with overlapping neighbourhoods are counted
                                     together and share the 2-hop lists they read in L2 (unsorted rows
-                                    give an arbitrary order); 2 vertex order. Same counts in every mode.
+                                    give an arbitrary order), and the thread-block work items are laid
+                                    out in the order of their first out-neighbour's id (with rows sorted
+                                    by id, an item's out-neighbours span a contiguous id range, so items
+                                    that run at the same time read overlapping 2-hop lists); 2 vertex
+                                    order. Same counts in every mode.
                                     Single-graph calls: tc_count, tc_count_async, tc_count_host on a CSR
                                     with fewer than 2^31 entries, and tc_count_dag, whose key takes the
                                     first out-neighbour (the smallest of N+(u) for sorted lists); batches

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI declared in include/tc.h: contexts, workspace, the
 // single-graph entry points, statistics and diagnostics. Batched counting
 // lives in batch.cu, serving in serve.cu.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -296,10 +297,17 @@ static tc_status enqueue_count(tc_ctx* ctx, Workspace& ws, const int32_t* dag_pt
     long long nl = 0;
     if (per_vertex && n > 0) e = cudaMemsetAsync(per_vertex, 0, (size_t)n * 8, st);
     if (e == cudaSuccess && n > 0) {
-        const int64_t m_cap = ws.items.bytes / sizeof(int2);
+        int64_t m_cap = ws.items.bytes / sizeof(int2);
+        // ordered work items: binning writes into items2, then placement into items
+        const bool order_items = BLOCK_ITEM_ORDER && ncol && ws.items2.p && ws.ikey.p;
+        if (order_items) {
+            const int64_t c2 = (int64_t)(ws.items2.bytes / sizeof(int2)), c3 = (int64_t)(ws.ikey.bytes / 4);
+            m_cap = std::min(m_cap, std::min(c2, c3));
+        }
         e = launch_bin(dag_ptr, n, ctx->cfg, (int32_t*)ws.warp_list.p, (int2*)ws.warp_desc.p, (int2*)ws.items.p,
                        m_cap, ctr, ctx->num_sms, st, &nl, dag_bnd, max_m, ncol, (int32_t*)ws.okey.p,
-                       (int32_t*)ws.ohist.p, (long long*)ws.partial.p);
+                       (int32_t*)ws.ohist.p, (long long*)ws.partial.p, order_items ? dag_col : nullptr,
+                       order_items ? (int32_t*)ws.ikey.p : nullptr, order_items ? (int2*)ws.items2.p : nullptr);
         timing_mark(tm, 2, st);
         if (e == cudaSuccess)
             e = launch_count(dag_ptr, dag_col, n, (const int32_t*)ws.warp_list.p, (const int2*)ws.warp_desc.p,
@@ -325,6 +333,11 @@ static tc_status order_keys(tc_ctx* ctx, Workspace& ws, int64_t n, int64_t nnz, 
     if ((s = ws.okey.ensure(ctx, (size_t)(n + 1) * 4, st))) return s;
     if ((s = ws.ohist.ensure(ctx, (size_t)(n + 1) * 4, st))) return s;
     if ((s = ws.partial.ensure(ctx, (size_t)(scan_blocks(n) + 2) * 8, st))) return s;
+    if (BLOCK_ITEM_ORDER) {
+        const size_t cap = (size_t)item_capacity(n, nnz / 2, ctx->cfg.item_neighbors);
+        if ((s = ws.ikey.ensure(ctx, cap * 4, st))) return s;
+        if ((s = ws.items2.ensure(ctx, cap * sizeof(int2), st))) return s;
+    }
     *ncol = col;
     return TC_OK;
 }

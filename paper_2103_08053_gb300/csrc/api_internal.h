@@ -29,9 +29,10 @@ struct Workspace {
     DevBuf deg, kept, partial, dag_ptr, dag_col, warp_list, warp_desc, items, ctr, stats, hubs, kbits, bnd;
     DevBuf pc;  // physical-combination scratch (tc_params.balance == TC_BALANCE_PC only)
     DevBuf okey, ohist;  // ordered warp list: per-vertex locality keys, key histogram / offsets
+    DevBuf ikey, items2; // ordered work items (BLOCK_ITEM_ORDER): item keys, items as binned
     void release_all(tc_ctx* ctx) {
         for (DevBuf* b : {&deg, &kept, &partial, &dag_ptr, &dag_col, &warp_list, &warp_desc, &items, &ctr, &stats,
-                          &hubs, &kbits, &bnd, &pc, &okey, &ohist})
+                          &hubs, &kbits, &bnd, &pc, &okey, &ohist, &ikey, &items2})
             b->release(ctx);
     }
 };

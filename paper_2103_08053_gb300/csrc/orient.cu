@@ -518,8 +518,10 @@ __global__ void __launch_bounds__(SCAN_THREADS)
     if (threadIdx.x == 0) partial[blockIdx.x] = tot;
 }
 
-// to_warp_count: the scan is of the ordered warp list's key histogram, whose
-// total is the warp list's length (else the DAG offsets: total = m).
+// to_warp_count: 1, the scan is of the ordered warp list's key histogram, whose
+// total is the warp list's length; 2, of the ordered work items' key
+// histogram (the total, the item count, is known already); 0, the DAG
+// offsets (total = m).
 __global__ void __launch_bounds__(SCAN_TOP_THREADS)
     k_scan_top(long long* __restrict__ partial, int nb, int32_t* __restrict__ out, int64_t n, DevCounters* ctr,
                int to_warp_count) {
@@ -536,9 +538,9 @@ __global__ void __launch_bounds__(SCAN_TOP_THREADS)
         pre += x;
     }
     if (threadIdx.x == 0) {
-        if (to_warp_count) {
+        if (to_warp_count == 1) {
             ctr->n_warp = (int)tot;  // <= n < 2^31
-        } else {
+        } else if (to_warp_count == 0) {
             ctr->m = tot;
             if (tot > 0x7fffffffLL) atomicOr(&ctr->err, ERRBIT_DAG_TOO_BIG);
             out[n] = (int32_t)tot;
@@ -641,6 +643,33 @@ __global__ void k_bin(const int32_t* __restrict__ dag_ptr, const int2* __restric
             }
         }
     }
+}
+
+// Ordered work items: the key of item i (u, first out-neighbour index j) is the
+// id of N+(u)[j], counted into the (zeroed) histogram; items2 holds the items
+// as binning wrote them.
+__global__ void k_item_key(const int32_t* __restrict__ dag_ptr, const int2* __restrict__ dag_bnd,
+                           const int32_t* __restrict__ dcol, const int2* __restrict__ items2, int32_t* __restrict__ ikey,
+                           int32_t* __restrict__ ohist, int64_t n, DevCounters* ctr) {
+    if (ctr->err) return;
+    const int ni = ctr->n_items;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x) {
+        const int2 it = items2[i];
+        const int a = dag_bnd ? dag_bnd[it.x].x : dag_ptr[it.x];
+        int key = __ldg(dcol + a + it.y);
+        if ((unsigned)key >= (unsigned long long)n) key = 0;  // a bad id is reported by the counting kernels
+        ikey[i] = key;
+        atomicAdd(&ohist[key], 1);
+    }
+}
+
+// Ordered work items, placement: item i takes the next slot of its key's run.
+__global__ void k_item_place(const int2* __restrict__ items2, const int32_t* __restrict__ ikey,
+                             int32_t* __restrict__ ohist, int2* __restrict__ items, DevCounters* ctr) {
+    if (ctr->err) return;
+    const int ni = ctr->n_items;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ni; i += gridDim.x * blockDim.x)
+        items[atomicAdd(&ohist[ikey[i]], 1)] = items2[i];
 }
 
 // Ordered warp list, second pass: every warp-class vertex takes the next slot
@@ -772,9 +801,13 @@ cudaError_t launch_orient_row_local_pieces(const void* row_ptr, int offset_bits,
 cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* warp_desc,
                        int2* items, int64_t item_cap, DevCounters* ctr, int num_sms, cudaStream_t st,
                        long long* launches, const int2* dag_bnd, long long max_m, const int32_t* ncol,
-                       int32_t* okey, int32_t* ohist, long long* partial) {
+                       int32_t* okey, int32_t* ohist, long long* partial, const int32_t* dcol, int32_t* ikey,
+                       int2* items2) {
     if (n <= 0) return cudaSuccess;
     if (!ncol) okey = nullptr;
+    const bool order_items = okey && dcol && ikey && items2;
+    int2* items_out = items;
+    if (order_items) items = items2;  // binning writes here; the placement pass fills items_out
     int g = (int)((n + 255) / 256);
     if (g > num_sms * 16) g = num_sms * 16;
     if (okey) {
@@ -792,6 +825,16 @@ cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, i
     k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(ohist, n, partial, ohist);
     k_place<<<g, 256, 0, st>>>(dag_ptr, dag_bnd, n, cfg.warp_max_out_degree, cfg.shard_count, cfg.shard_index, okey,
                                ohist, warp_list, warp_desc, ctr);
+    if (!order_items) return cudaGetLastError();
+    const cudaError_t e = cudaMemsetAsync(ohist, 0, (size_t)n * 4, st);
+    if (e != cudaSuccess) return e;
+    *launches += 5;
+    const int ig = num_sms * 8;
+    k_item_key<<<ig, 256, 0, st>>>(dag_ptr, dag_bnd, dcol, items2, ikey, ohist, n, ctr);
+    k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(ohist, n, partial);
+    k_scan_top<<<1, SCAN_TOP_THREADS, 0, st>>>(partial, nb, ohist, n, ctr, 2);
+    k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(ohist, n, partial, ohist);
+    k_item_place<<<ig, 256, 0, st>>>(items2, ikey, ohist, items_out, ctr);
     return cudaGetLastError();
 }
 

@@ -124,11 +124,21 @@ cudaError_t launch_orient_batch(const GraphRef* graphs, int k, int offset_bits, 
 // scan_blocks(n) + 2 long longs): the warp list is laid out in the order of a
 // locality key, min(u, first entry of u's row) -- a histogram of the keys,
 // its scan, and a placement pass -- instead of in vertex order.
+// Ordered work items (with the ordered warp list; dcol: the DAG's entries,
+// ikey: item_cap ints, items2: item_cap int2 of scratch): the thread-block
+// work items are laid out in the order of their first out-neighbour's id --
+// rows sorted by id give an item a contiguous id range of out-neighbours, so
+// items that run at the same time read overlapping 2-hop lists.
 cudaError_t launch_bin(const int32_t* dag_ptr, int64_t n, const CountCfg& cfg, int32_t* warp_list, int2* warp_desc,
                        int2* items, int64_t item_cap, DevCounters* ctr, int num_sms, cudaStream_t st,
                        long long* launches,
                        const int2* dag_bnd = nullptr, long long max_m = -1, const int32_t* ncol = nullptr,
-                       int32_t* okey = nullptr, int32_t* ohist = nullptr, long long* partial = nullptr);
+                       int32_t* okey = nullptr, int32_t* ohist = nullptr, long long* partial = nullptr,
+                       const int32_t* dcol = nullptr, int32_t* ikey = nullptr, int2* items2 = nullptr);
+
+#ifndef BLOCK_ITEM_ORDER
+#define BLOCK_ITEM_ORDER 1  // 1: thread-block work items ordered by their first out-neighbour (ordered mode)
+#endif
 
 // ---- counting (count.cu) ----------------------------------------------------
 cudaError_t launch_count(const int32_t* dag_ptr, const int32_t* dag_col, int64_t n, const int32_t* warp_list,

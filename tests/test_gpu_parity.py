@@ -361,8 +361,10 @@ def test_shards_sum_to_total(T, warp_order):
 
 def test_ordered_warp_list_launches_and_host_pieces(T):
     # warp_order 1: binning gives every warp-class vertex a locality key and
-    # becomes histogram + 3 scan kernels + placement (4 more launches); the
-    # piecewise host path (>= 2^20 entries) takes the same order
+    # becomes histogram + 3 scan kernels + placement (4 more launches), and the
+    # thread-block work items are ordered by key too (item keys + 3 scan
+    # kernels + placement: 5 more); the piecewise host path (>= 2^20 entries)
+    # takes the same order
     g = G.rmat(13, 16, seed=20)
     big = G.disjoint_union([G.rgg(30_001, 40.0, seed=35), G.star(5000), G.wheel(700),
                             G.rmat(14, 16, seed=36), G.complete(45)])
@@ -370,7 +372,7 @@ def test_ordered_warp_list_launches_and_host_pieces(T):
         rp, col = dev(g)
         l0 = c.kernel_launches()
         assert c.count(g.n, rp, col) == oracle.count(g)
-        assert c.kernel_launches() - l0 == 12
+        assert c.kernel_launches() - l0 == 17
         assert gpu_count(c, G.shuffle_rows(g, 3)) == oracle.count(g)   # unsorted rows: an arbitrary order
         # a compact DAG (tc_orient) counted with the ordered list, per vertex
         d = c.orient(g.n, rp, col)
@@ -378,7 +380,7 @@ def test_ordered_warp_list_launches_and_host_pieces(T):
         l1 = c.kernel_launches()
         want_total, want_pv = oracle.count_dag(oracle.orient(g), per_vertex=True)
         assert c.count_dag(d, per_vertex=pv) == want_total
-        assert c.kernel_launches() - l1 == 8      # ordered binning (5) + 3 counting
+        assert c.kernel_launches() - l1 == 13     # ordered binning (5) + item ordering (5) + 3 counting
         assert np.array_equal(pv.cpu().numpy().astype(np.uint64), want_pv)
         d.free()
         want = oracle.count(big)
