@@ -815,7 +815,7 @@ __device__ __forceinline__ uint32_t vc_range_quad(int s, int e, int nq, int tab,
 // groups of eight entries); the combined octet indices [skip, min(limit,
 // total)) are dealt one per lane per step, each read with one 256-bit load;
 // slots outside their list are masked. *done = octets processed.
-template <int HM, int SL, bool OVF, bool CHAIN, bool FILT = false>
+template <int HM, int SL, bool OVF, bool CHAIN, bool FILT = false>  // FILT: HM == 0, SL == 4
 __device__ __forceinline__ uint32_t vc_range_oct(int s, int e, int no, int tab, int lgB, int skip, int limit,
                                                  const int32_t* __restrict__ dag_col, int m, int lane,
                                                  int stage, int* done, unsigned mult, int sig = 0) {
@@ -869,21 +869,31 @@ __device__ __forceinline__ uint32_t vc_range_oct(int s, int e, int no, int tab, 
         }
         int more = 0;  // bit j: slot j's bucket may have sent its key on and did not match
         if constexpr (!CHAIN && FILT) {
+            static_assert(HM == 0 && SL == 4, "signatures: multiplicative hash, 4-slot buckets");
             // overflow-free table with bucket signatures (int offset sig): every
-            // slot's signature word is read (4 bytes), and only the list's slots
-            // whose bit is set load their bucket (16 bytes)
-            int hb[8];
+            // slot reads its signature word (4 bytes); h = w * mult gives the
+            // bucket (top lgB bits) and the signature bit (the five bits below:
+            // rotating the word by h >> (27 - lgB), which the rotate takes mod
+            // 32, brings it to bit 0). Only the list's slots whose bit is set
+            // then load their bucket (16 bytes), one set bit per round, the key
+            // picked from the octet by the bit's index
             unsigned pass = 0;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                hb[j] = bucket_of<HM>(k.v[j], lgB, mult);
-                const unsigned sw = (unsigned)g_smem[sig + hb[j]];
-                pass |= ((sw >> sig_bit<HM>(k.v[j], lgB, mult)) & 1u) << j;
+                const unsigned h = (unsigned)k.v[j] * mult;
+                const unsigned sw = (unsigned)g_smem[sig + (int)(h >> (32 - lgB))];
+                pass |= (__funnelshift_r(sw, sw, h >> (27 - lgB)) & 1u) << j;
             }
             pass &= slot_mask<8>(lo, hi);
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if (pass & (1u << j)) hits += Bucket<SL>::at(tab, hb[j]).match(k.v[j]);
+            while (pass) {
+                const int j = __ffs(pass) - 1;
+                pass &= pass - 1;
+                const int k01 = (j & 1) ? k.v[1] : k.v[0], k23 = (j & 1) ? k.v[3] : k.v[2];
+                const int k45 = (j & 1) ? k.v[5] : k.v[4], k67 = (j & 1) ? k.v[7] : k.v[6];
+                const int k03 = (j & 2) ? k23 : k01, k47 = (j & 2) ? k67 : k45;
+                const int w = (j & 4) ? k47 : k03;
+                hits += Bucket<4>::at(tab, (int)(((unsigned)w * mult) >> (32 - lgB))).match(w);
+            }
         } else if constexpr (!CHAIN) {
             // overflow-free table: every slot is probed and the mask keeps the list's
             unsigned mb = 0;
@@ -1351,7 +1361,7 @@ __global__ void __launch_bounds__(1024, 1)
                 }
                 mult = hash_mult(attempt + 1);
             }
-            constexpr bool kFilter = BLOCK_FILTER && BLOCK_SLOTS == 4;
+            constexpr bool kFilter = BLOCK_FILTER && BLOCK_SLOTS == 4 && HM == 0;  // x mod B tables always chain
             if (kFilter && !chained) {
                 // overflow-free: every key sits in its home bucket; the bucket's length
                 // word (no longer needed) becomes its signature
@@ -1393,7 +1403,7 @@ __global__ void __launch_bounds__(1024, 1)
                     int done = 0;
                     if (quad == 2) {
                         const int ej = j < cnt ? E[j] : 0;
-                        if (!chained)
+                        if (HM == 0 && !chained)  // x mod B tables always chain
                             h += vc_range_oct<HM, BLOCK_SLOTS, false, false, kFilter>(
                                 sj, ej, uj, table_off, lgB, F - base_flat, F1 - base_flat, dag_col, m, lane, stage,
                                 &done, mult, lenw);
