@@ -186,14 +186,17 @@ __device__ __forceinline__ int bucket_of(int w, int lgB, unsigned mult = kHashMu
     return (int)(((unsigned)w * mult) >> (32 - lgB));
 }
 
-// Signature bit of key w in a table of 2^lgB buckets (lgB <= 27): the five
-// hash bits below the bucket bits (multiplicative hash), or the five id bits
-// above them (x mod B). A bucket's signature word has the bits of its keys, so
-// a key whose bit is clear in its home bucket's word is not in the bucket.
+// Signature bit of key w in a table of 2^lgB buckets (lgB <= 27): with the
+// multiplicative hash h = w * mult, the five hash bits below the bucket bits,
+// r = (h >> (27 - lgB)) mod 32, minus one (mod 32) -- the bit that a right
+// rotation of the signature word by r brings to bit 31 (vc_range_oct_sig);
+// with x mod B, the five id bits above the bucket bits. A bucket's signature
+// word has the bits of its keys, so a key whose bit is clear in its home
+// bucket's word is not in the bucket.
 template <int HM>
 __device__ __forceinline__ int sig_bit(int w, int lgB, unsigned mult) {
     if (HM == 1) return (int)(((unsigned)w >> lgB) & 31u);
-    return (int)((((unsigned)w * mult) >> (27 - lgB)) & 31u);
+    return (int)(((((unsigned)w * mult) >> (27 - lgB)) + 31u) & 31u);
 }
 
 // ---- table builds (bucket-major buckets of SL slots) ------------------------
@@ -815,10 +818,10 @@ __device__ __forceinline__ uint32_t vc_range_quad(int s, int e, int nq, int tab,
 // groups of eight entries); the combined octet indices [skip, min(limit,
 // total)) are dealt one per lane per step, each read with one 256-bit load;
 // slots outside their list are masked. *done = octets processed.
-template <int HM, int SL, bool OVF, bool CHAIN, bool FILT = false>  // FILT: HM == 0, SL == 4
+template <int HM, int SL, bool OVF, bool CHAIN>
 __device__ __forceinline__ uint32_t vc_range_oct(int s, int e, int no, int tab, int lgB, int skip, int limit,
                                                  const int32_t* __restrict__ dag_col, int m, int lane,
-                                                 int stage, int* done, unsigned mult, int sig = 0) {
+                                                 int stage, int* done, unsigned mult) {
     const unsigned nem = __ballot_sync(FULL, no > 0);
     if (nem == 0) {
         *done = 0;
@@ -868,33 +871,7 @@ __device__ __forceinline__ uint32_t vc_range_oct(int s, int e, int no, int tab, 
             }
         }
         int more = 0;  // bit j: slot j's bucket may have sent its key on and did not match
-        if constexpr (!CHAIN && FILT) {
-            static_assert(HM == 0 && SL == 4, "signatures: multiplicative hash, 4-slot buckets");
-            // overflow-free table with bucket signatures (int offset sig): every
-            // slot reads its signature word (4 bytes); h = w * mult gives the
-            // bucket (top lgB bits) and the signature bit (the five bits below:
-            // rotating the word by h >> (27 - lgB), which the rotate takes mod
-            // 32, brings it to bit 0). Only the list's slots whose bit is set
-            // then load their bucket (16 bytes), one set bit per round, the key
-            // picked from the octet by the bit's index
-            unsigned pass = 0;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const unsigned h = (unsigned)k.v[j] * mult;
-                const unsigned sw = (unsigned)g_smem[sig + (int)(h >> (32 - lgB))];
-                pass |= (__funnelshift_r(sw, sw, h >> (27 - lgB)) & 1u) << j;
-            }
-            pass &= slot_mask<8>(lo, hi);
-            while (pass) {
-                const int j = __ffs(pass) - 1;
-                pass &= pass - 1;
-                const int k01 = (j & 1) ? k.v[1] : k.v[0], k23 = (j & 1) ? k.v[3] : k.v[2];
-                const int k45 = (j & 1) ? k.v[5] : k.v[4], k67 = (j & 1) ? k.v[7] : k.v[6];
-                const int k03 = (j & 2) ? k23 : k01, k47 = (j & 2) ? k67 : k45;
-                const int w = (j & 4) ? k47 : k03;
-                hits += Bucket<4>::at(tab, (int)(((unsigned)w * mult) >> (32 - lgB))).match(w);
-            }
-        } else if constexpr (!CHAIN) {
+        if constexpr (!CHAIN) {
             // overflow-free table: every slot is probed and the mask keeps the list's
             unsigned mb = 0;
 #pragma unroll
@@ -920,6 +897,89 @@ __device__ __forceinline__ uint32_t vc_range_oct(int s, int e, int no, int tab, 
             for (int j = 0; j < 8; ++j)
                 if ((more >> j) & 1)
                     hits += probe_next<SL, OVF>(tab, mask, bucket_of<HM>(k.v[j], lgB, mult), k.v[j]);
+        }
+    }
+    *done = end > skip ? end - skip : 0;
+    return hits;
+}
+
+// vc_range_oct for an overflow-free thread-block table with bucket
+// signatures (multiplicative hash, 4-slot buckets, int offset sig of the
+// signature words), for tables of 2^LGB buckets (LGB = 0: lgB given at run
+// time). Every slot reads its signature word: h = w * mult, the bucket is
+// h >> (32 - lgB), and a right rotation of the word by h >> (27 - lgB) (the
+// rotate takes the amount mod 32) brings the key's signature bit to bit 31,
+// which a funnel shift appends to the octet's pass bits. Only the list's
+// slots whose bit is set then load their bucket (16 bytes), one set bit per
+// round, the key picked from the octet by the bit's index. Lanes past the
+// combined range keep their last octet's keys with an empty slot mask.
+template <int LGB>
+__device__ __forceinline__ uint32_t vc_range_oct_sig(int s, int e, int no, int tab, int lgB_rt, int skip, int limit,
+                                                     const int32_t* __restrict__ dag_col, int m, int lane,
+                                                     int stage, int* done, unsigned mult, int sig) {
+    const int lgB = LGB ? LGB : lgB_rt;
+    const unsigned nem = __ballot_sync(FULL, no > 0);
+    if (nem == 0) {
+        *done = 0;
+        return 0;
+    }
+    const int c = __popc(nem);
+    if (no > 0) {
+        const int p = __popc(nem & lanemask_lt(lane));
+        g_smem[stage + p] = s;
+        g_smem[stage + 32 + p] = e;
+        g_smem[stage + 64 + p] = no;
+    }
+    __syncwarp();
+    const bool lst = lane < c;
+    const int cs = lst ? g_smem[stage + lane] : 0;
+    const int ce = lst ? g_smem[stage + 32 + lane] : 0;
+    const int co = lst ? g_smem[stage + 64 + lane] : 0;
+    __syncwarp();
+    const int P = warp_incl_scan(co, lane);
+    const int total = __shfl_sync(FULL, P, 31);
+    const int end = total < limit ? total : limit;
+    const int Pex = P - co;
+    const int obias = (cs >> 3) - Pex;
+    const unsigned le = lanemask_le(lane);
+    uint32_t hits = 0;
+    Octet k;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) k.v[j] = NOKEY;
+    for (int base = skip; base < end; base += 32) {
+        const int o = vc_owner(base, P, Pex, lst, le) & 31;
+        const int ob = __shfl_sync(FULL, obias, o);
+        const int so = __shfl_sync(FULL, cs, o);
+        const int eo = __shfl_sync(FULL, ce, o);
+        const int f = base + lane;
+        const int x0 = 8 * (ob + f);  // dag_col index of the octet's first slot
+        unsigned msk = 0;
+        if (f < end) {
+            msk = slot_mask<8>(so - x0, eo - x0);
+            if (x0 + 7 < m) {
+                k = ld_octet(dag_col + x0);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 7; ++j)
+                    if (x0 + j < m) k.v[j] = __ldg(dag_col + x0 + j);
+            }
+        }
+        unsigned pass = 0;
+#pragma unroll
+        for (int j = 7; j >= 0; --j) {
+            const unsigned h = (unsigned)k.v[j] * mult;
+            const unsigned sw = (unsigned)g_smem[sig + (int)(h >> (32 - lgB))];
+            pass = __funnelshift_lc(__funnelshift_r(sw, sw, h >> (27 - lgB)), pass, 1);
+        }
+        pass &= msk;
+        while (pass) {
+            const int j = 31 - __clz(pass);
+            pass ^= 1u << j;
+            const int k01 = (j & 1) ? k.v[1] : k.v[0], k23 = (j & 1) ? k.v[3] : k.v[2];
+            const int k45 = (j & 1) ? k.v[5] : k.v[4], k67 = (j & 1) ? k.v[7] : k.v[6];
+            const int k03 = (j & 2) ? k23 : k01, k47 = (j & 2) ? k67 : k45;
+            const int w = (j & 4) ? k47 : k03;
+            hits += Bucket<4>::at(tab, (int)(((unsigned)w * mult) >> (32 - lgB))).match(w);
         }
     }
     *done = end > skip ? end - skip : 0;
@@ -1403,10 +1463,27 @@ __global__ void __launch_bounds__(1024, 1)
                     int done = 0;
                     if (quad == 2) {
                         const int ej = j < cnt ? E[j] : 0;
-                        if (HM == 0 && !chained)  // x mod B tables always chain
-                            h += vc_range_oct<HM, BLOCK_SLOTS, false, false, kFilter>(
-                                sj, ej, uj, table_off, lgB, F - base_flat, F1 - base_flat, dag_col, m, lane, stage,
-                                &done, mult, lenw);
+                        if (kFilter && !chained) {
+                            // table sizes 2^6 .. 2^13 buckets with constant shifts
+#define TC_OCT_SIG(L)                                                                                       \
+    vc_range_oct_sig<L>(sj, ej, uj, table_off, lgB, F - base_flat, F1 - base_flat, dag_col, m, lane, stage, \
+                        &done, mult, lenw)
+                            switch (lgB) {
+                                case 6: h += TC_OCT_SIG(6); break;
+                                case 7: h += TC_OCT_SIG(7); break;
+                                case 8: h += TC_OCT_SIG(8); break;
+                                case 9: h += TC_OCT_SIG(9); break;
+                                case 10: h += TC_OCT_SIG(10); break;
+                                case 11: h += TC_OCT_SIG(11); break;
+                                case 12: h += TC_OCT_SIG(12); break;
+                                case 13: h += TC_OCT_SIG(13); break;
+                                default: h += TC_OCT_SIG(0); break;
+                            }
+#undef TC_OCT_SIG
+                        } else if (HM == 0 && !chained)  // x mod B tables always chain
+                            h += vc_range_oct<HM, BLOCK_SLOTS, false, false>(sj, ej, uj, table_off, lgB,
+                                                                             F - base_flat, F1 - base_flat, dag_col,
+                                                                             m, lane, stage, &done, mult);
                         else
                             h += vc_range_oct<HM, BLOCK_SLOTS, BLOCK_OVF, true>(sj, ej, uj, table_off, lgB,
                                                                                 F - base_flat, F1 - base_flat,
