@@ -42,10 +42,13 @@ GOLDEN = os.path.join(ROOT, "tests", "golden")
 # single-graph workloads (--workload); the default is the largest one
 WORKLOADS = {
     "rmat26": dict(name="rmat-s26-ef16-seed3", graph="rmat26", offset_bits=64, golden="rmat26.json",
-                   oracle_fraction=1 / 32),
-    "rgg22": dict(name="rgg-2^22-meandeg64-seed2", graph="rgg22", offset_bits=32, oracle_fraction=1.0),
-    "rmat16": dict(name="rmat-s16-ef16-seed1", graph="rmat16", offset_bits=32, oracle_fraction=1.0),
-    "rmat22": dict(name="rmat-s22-ef16-seed1", graph="rmat22", offset_bits=32, oracle_fraction=1.0),
+                   oracle_fraction=1 / 32, n=1 << 26, nnz_max=2 * 16 << 26),
+    "rgg22": dict(name="rgg-2^22-meandeg64-seed2", graph="rgg22", offset_bits=32, oracle_fraction=1.0,
+                  n=1 << 22, nnz_max=80 << 22),
+    "rmat16": dict(name="rmat-s16-ef16-seed1", graph="rmat16", offset_bits=32, oracle_fraction=1.0,
+                   n=1 << 16, nnz_max=2 * 16 << 16),
+    "rmat22": dict(name="rmat-s22-ef16-seed1", graph="rmat22", offset_bits=32, oracle_fraction=1.0,
+                   n=1 << 22, nnz_max=2 * 16 << 22),
 }
 DEFAULT_WORKLOAD = "rmat26"
 # the reference arm's per-step sample of the main workload's vertices
@@ -467,28 +470,56 @@ class HugePinned:
     """A page-locked host copy of a large numpy array in 2 MiB pages: anonymous
     memory mapped with madvise(MADV_HUGEPAGE), filled, then registered with
     cudaHostRegister. On the GB300 machine the copy engine read such buffers at
-    209-211 GB/s, while multi-GB buffers from the page-locked allocator, made
-    after the graph generation had churned host memory, were read at 50-210
-    GB/s from one process to the next. `array` is the host view; close()
-    unregisters and unmaps."""
+    209-211 GB/s when (nearly) all of them sat in 2 MiB pages, and at 18-65
+    GB/s when 4-11 % of them had fallen back to 4 KiB pages, which happens when
+    they are first touched after the graph generation has churned host memory;
+    HugePinned.reserve() maps and touches a region before that, and the
+    constructor fills a reserved region when one large enough is given.
+    `array` is the host view; close() unregisters and unmaps."""
 
-    def __init__(self, torch, a):
+    _libc = None
+
+    @classmethod
+    def _c(cls):
+        import ctypes
+        if cls._libc is None:
+            libc = ctypes.CDLL("libc.so.6", use_errno=True)
+            libc.mmap.restype = ctypes.c_void_p
+            libc.mmap.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_long]
+            libc.madvise.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+            libc.munmap.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
+            libc.memset.restype = ctypes.c_void_p
+            libc.memset.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t]
+            cls._libc = libc
+        return cls._libc
+
+    @classmethod
+    def reserve(cls, nbytes: int):
+        """Map `nbytes` (rounded up to 2 MiB) of anonymous memory, advise huge
+        pages and touch every page now. Returns (ptr, nbytes)."""
+        import ctypes
+        libc = cls._c()
+        nbytes = max((int(nbytes) + (2 << 20) - 1) // (2 << 20) * (2 << 20), 2 << 20)
+        p = libc.mmap(None, nbytes, 3, 0x22, -1, 0)  # PROT_READ|PROT_WRITE, MAP_PRIVATE|MAP_ANONYMOUS
+        if p in (None, ctypes.c_void_p(-1).value):
+            raise MemoryError("mmap failed")
+        libc.madvise(p, nbytes, 14)  # MADV_HUGEPAGE (advice only; 4 KiB pages still work)
+        libc.memset(p, 0, nbytes)
+        return p, nbytes
+
+    def __init__(self, torch, a, region=None):
         import ctypes
 
         import numpy as np
-        self._libc = ctypes.CDLL("libc.so.6", use_errno=True)
-        self._libc.mmap.restype = ctypes.c_void_p
-        self._libc.mmap.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                    ctypes.c_long]
-        self._libc.madvise.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
-        self._libc.munmap.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
         self._cudart = torch.cuda.cudart()
-        self.nbytes = max((a.nbytes + (2 << 20) - 1) // (2 << 20) * (2 << 20), 2 << 20)
-        p = self._libc.mmap(None, self.nbytes, 3, 0x22, -1, 0)  # PROT_READ|PROT_WRITE, MAP_PRIVATE|MAP_ANONYMOUS
-        if p in (None, ctypes.c_void_p(-1).value):
-            raise MemoryError("mmap failed")
-        self.ptr = p
-        self._libc.madvise(p, self.nbytes, 14)  # MADV_HUGEPAGE (advice only; 4 KiB pages still work)
+        if region is not None and region[1] >= a.nbytes:
+            self.ptr, self.nbytes = region
+        else:
+            if region is not None:
+                self._c().munmap(region[0], region[1])
+            self.ptr, self.nbytes = self.reserve(a.nbytes)
+        p = self.ptr
         buf = (ctypes.c_char * self.nbytes).from_address(p)
         self.array = np.frombuffer(buf, dtype=a.dtype, count=a.size)
         self.array[:] = a.reshape(-1)
@@ -518,11 +549,12 @@ class HugePinned:
             if self.registered:
                 self._cudart.cudaHostUnregister(self.ptr)
             self.array = None
-            self._libc.munmap(self.ptr, self.nbytes)
+            self._c().munmap(self.ptr, self.nbytes)
             self.ptr = None
 
 
-def measure_graph(T, torch, dev, key, spec, g, steps, warmup, rank, world, dist, e2e_steps, clocks):
+def measure_graph(T, torch, dev, key, spec, g, steps, warmup, rank, world, dist, e2e_steps, clocks,
+                  regions=(None, None)):
     """Time `steps` device steps (tc_count_async) of graph g after `warmup`
     untimed ones, then the end-to-end call (tc_count_host from pinned host
     memory, copies inside the timed region). Returns the line's keys, the
@@ -582,7 +614,7 @@ def measure_graph(T, torch, dev, key, spec, g, steps, warmup, rank, world, dist,
 
     # end to end through the C ABI from pinned host memory: H2D of the CSR, the
     # whole path, D2H of the count, every step
-    rp_hp, col_hp = HugePinned(torch, rp_h), HugePinned(torch, col_h)
+    rp_hp, col_hp = HugePinned(torch, rp_h, regions[0]), HugePinned(torch, col_h, regions[1])
     rp_pin, col_pin = torch.from_numpy(rp_hp.array), torch.from_numpy(col_hp.array)
     for _ in range(3):
         ctx.count_host(g.n, rp_pin.numpy(), col_pin.numpy(), stream=stream)
@@ -722,12 +754,17 @@ def run_gb300(args):
     spec = WORKLOADS[key]
     single = world == 1
 
+    # host buffers of the end-to-end calls, mapped and touched before the
+    # graph generation churns host memory, so that they get 2 MiB pages
+    regions = host_regions(spec)
+    regions2 = host_regions(WORKLOADS["rgg22"]) if single and args.second and key != "rgg22" else (None, None)
     t0 = time.time()
     g = make_graph(spec)
     g.name = spec["name"]
     log(f"[rank {rank}] generated {spec['name']}: n={g.n} m={g.m} in {time.time() - t0:.1f}s")
     main, (rp, col), total = measure_graph(T, torch, dev, key, spec, g, args.steps, args.warmup, rank, world,
-                                           dist, e2e_steps=max(3, min(args.steps, args.e2e_steps)), clocks=True)
+                                           dist, e2e_steps=max(3, min(args.steps, args.e2e_steps)), clocks=True,
+                                           regions=regions)
     log(f"[rank {rank}] {spec['name']}: {main['ms_per_step']:.2f} ms per step")
     result = {
         "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -773,7 +810,7 @@ def run_gb300(args):
         g2 = make_graph(s2)
         g2.name = s2["name"]
         line2, (rp2, col2), total2 = measure_graph(T, torch, dev, "rgg22", s2, g2, 50, 5, 0, 1, None, e2e_steps=10,
-                                                   clocks=False)
+                                                   clocks=False, regions=regions2)
         import oracle
         t = time.perf_counter()
         want2 = oracle.count(g2, threads=oracle.max_threads())
@@ -813,6 +850,13 @@ def run_gb300(args):
     if dist:
         dist.destroy_process_group()
     print(json.dumps(result), flush=True)
+
+
+def host_regions(spec):
+    """HugePinned reservations for a workload's row offsets and neighbour
+    lists, sized by the workload's bounds on n and nnz."""
+    bits = spec["offset_bits"]
+    return (HugePinned.reserve((spec["n"] + 1) * bits // 8), HugePinned.reserve(spec["nnz_max"] * 4))
 
 
 def make_graph_tensors(torch, dev, g):
