@@ -669,36 +669,46 @@ __device__ __forceinline__ uint32_t vc_pack_oct(int s, int l, int td,
     }
     int cum = 0;
     int run_slot = 0, run_hits = 0;  // per-vertex hits per run of one pack slot (as in vc_pack_quad)
-    for (int base = 0; base < total; base += 32) {
+    // the octet of window base + 32 is loaded while window base is probed;
+    // lanes past the combined range keep their last keys with an empty mask
+    Octet k, kn;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) kn.v[j] = NOKEY;
+    int lon = 8, hin = 0, kdn = 0;
+    auto fetch = [&](int b) {
         int o;
         if (use_bm) {
-            const unsigned w0 = bm[base >> 5];
+            const unsigned w0 = bm[b >> 5];
             o = (cum + __popc(w0 & le) - 1) & 31;
             cum += __popc(w0);
         } else {
-            o = vc_owner(base, P, Pex, lst, le) & 31;
+            o = vc_owner(b, P, Pex, lst, le) & 31;
         }
         const int ob = __shfl_sync(FULL, obias, o);
         const int so = __shfl_sync(FULL, cs, o);
         const int eo = __shfl_sync(FULL, ce, o);
-        const int kd = __shfl_sync(FULL, ctd, o);
-        const int f = base + lane;
+        kdn = __shfl_sync(FULL, ctd, o);
+        const int f = b + lane;
         const int x0 = 8 * (ob + f);  // dag_col index of the octet's first slot
-        Octet k;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) k.v[j] = NOKEY;
-        int lo = 8, hi = 0;
+        lon = 8;
+        hin = 0;
         if (f < total) {
-            lo = so - x0;
-            hi = eo - x0;
+            lon = so - x0;
+            hin = eo - x0;
             if (x0 + 7 < m) {
-                k = ld_octet(dag_col + x0);
+                kn = ld_octet(dag_col + x0);
             } else {
 #pragma unroll
                 for (int j = 0; j < 7; ++j)
-                    if (x0 + j < m) k.v[j] = __ldg(dag_col + x0 + j);
+                    if (x0 + j < m) kn.v[j] = __ldg(dag_col + x0 + j);
             }
         }
+    };
+    if (total > 0) fetch(0);
+    for (int base = 0; base < total; base += 32) {
+        k = kn;
+        const int lo = lon, hi = hin, kd = kdn;
+        if (base + 32 < total) fetch(base + 32);
         const int lg = (kd >> 16) & 31;
         const int tab = kd & 0xffff;
         unsigned mb = 0;  // bit j: slot j matched (every slot is probed; the mask keeps the list's)
@@ -943,27 +953,35 @@ __device__ __forceinline__ uint32_t vc_range_oct_sig(int s, int e, int no, int t
     const int obias = (cs >> 3) - Pex;
     const unsigned le = lanemask_le(lane);
     uint32_t hits = 0;
-    Octet k;
+    // the octet of window base + 32 is loaded while window base is probed
+    Octet k, kn;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) k.v[j] = NOKEY;
-    for (int base = skip; base < end; base += 32) {
-        const int o = vc_owner(base, P, Pex, lst, le) & 31;
+    for (int j = 0; j < 8; ++j) kn.v[j] = NOKEY;
+    unsigned mskn = 0;
+    auto fetch = [&](int b) {
+        const int o = vc_owner(b, P, Pex, lst, le) & 31;
         const int ob = __shfl_sync(FULL, obias, o);
         const int so = __shfl_sync(FULL, cs, o);
         const int eo = __shfl_sync(FULL, ce, o);
-        const int f = base + lane;
+        const int f = b + lane;
         const int x0 = 8 * (ob + f);  // dag_col index of the octet's first slot
-        unsigned msk = 0;
+        mskn = 0;
         if (f < end) {
-            msk = slot_mask<8>(so - x0, eo - x0);
+            mskn = slot_mask<8>(so - x0, eo - x0);
             if (x0 + 7 < m) {
-                k = ld_octet(dag_col + x0);
+                kn = ld_octet(dag_col + x0);
             } else {
 #pragma unroll
                 for (int j = 0; j < 7; ++j)
-                    if (x0 + j < m) k.v[j] = __ldg(dag_col + x0 + j);
+                    if (x0 + j < m) kn.v[j] = __ldg(dag_col + x0 + j);
             }
         }
+    };
+    if (skip < end) fetch(skip);
+    for (int base = skip; base < end; base += 32) {
+        k = kn;
+        const unsigned msk = mskn;
+        if (base + 32 < end) fetch(base + 32);
         unsigned pass = 0;
 #pragma unroll
         for (int j = 7; j >= 0; --j) {
