@@ -69,6 +69,27 @@ __global__ void k_degree(GraphRef one, const GraphRef* __restrict__ gs, int k, i
     }
 }
 
+// L2 eviction hints (PTX createpolicy + ld.global.nc.L2::cache_hint). The
+// orientation passes stream the neighbour lists once and gather a neighbour's
+// degree for every entry: the lists are read evict-first and the degree
+// gathers evict-last, so the streamed lists do not push the (much smaller)
+// degree array out of L2.
+__device__ __forceinline__ uint64_t l2_policy_last() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_first() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ int ldg_hint(const int32_t* a, uint64_t pol) {
+    int v;
+    asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(pol));
+    return v;
+}
+
 constexpr int ORIENT_THREADS = 256;
 constexpr int ORIENT_WARPS = ORIENT_THREADS / 32;
 constexpr int ORIENT_UNROLL = 4;
@@ -171,6 +192,7 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
         const int tot = __shfl_sync(FULL, P, 31);
         const int Pex = P - cl;
         const long long bias = ca - Pex;  // col index of combined entry f of this row: bias + f
+        const uint64_t pol_stream = l2_policy_first(), pol_keep = l2_policy_last();
         int cnt = (COMPACT && lst) ? dag_ptr[row0 + rid] : 0;  // compaction: the row's next output position
         for (int b0 = 0; b0 < tot; b0 += 32 * ORIENT_UNROLL) {
             // every load of the step first: ORIENT_UNROLL col reads, then their
@@ -184,14 +206,14 @@ __global__ void __launch_bounds__(ORIENT_THREADS)
                 oq[q] = o;
                 const int f = bw + lane;
                 atq[q] = __shfl_sync(FULL, bias, o) + f;
-                vq[q] = (f < tot) ? __ldg(col + atq[q]) : -1;
+                vq[q] = (f < tot) ? ldg_hint(col + atq[q], pol_stream) : -1;
             }
             // the compaction pass reads the count pass's keep bits instead of
             // gathering the neighbours' degrees again
             const bool gather = !(COMPACT && kbits);
 #pragma unroll
             for (int q = 0; q < ORIENT_UNROLL; ++q)
-                dq[q] = (gather && (unsigned)vq[q] < (unsigned long long)n) ? __ldg(deg + vb + vq[q]) : 0;
+                dq[q] = (gather && (unsigned)vq[q] < (unsigned long long)n) ? ldg_hint(deg + vb + vq[q], pol_keep) : 0;
 #pragma unroll
             for (int q = 0; q < ORIENT_UNROLL; ++q) {
                 const int bw = b0 + 32 * q;
@@ -295,6 +317,7 @@ __global__ void __launch_bounds__(HUB_THREADS)
         const Off* rp = static_cast<const Off*>(G.row_ptr);
         const long long a = (long long)rp[u], b = (long long)rp[u + 1];  // checked by k_degree
         const int du = deg[ug];
+        const uint64_t pol_stream = l2_policy_first(), pol_keep = l2_policy_last();
         if (threadIdx.x == 0) s_carry = 0;
         __syncthreads();
         // output: the compacted DAG, or (row-local count pass) the row itself
@@ -309,7 +332,7 @@ __global__ void __launch_bounds__(HUB_THREADS)
             int v[4], keepc = 0;
             bool kq[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) v[q] = (e0 + q < b) ? __ldg(G.col + e0 + q) : -1;
+            for (int q = 0; q < 4; ++q) v[q] = (e0 + q < b) ? ldg_hint(G.col + e0 + q, pol_stream) : -1;
             const bool from_bits = COMPACT && kbits;  // keep decisions of the count pass
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -320,7 +343,7 @@ __global__ void __launch_bounds__(HUB_THREADS)
                     } else if ((unsigned)v[q] >= (unsigned long long)G.n) {
                         atomicOr(&ctr->err, ERRBIT_BAD_GRAPH);
                     } else {
-                        const int dv = __ldg(deg + G.vbase + v[q]);
+                        const int dv = ldg_hint(deg + G.vbase + v[q], pol_keep);
                         kq[q] = (dv > du) || (dv == du && (int64_t)v[q] > u);
                     }
                 }
