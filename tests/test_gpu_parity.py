@@ -325,6 +325,27 @@ def test_param_regimes(T, name):
             assert gpu_count(c, g) == oracle.count(g), (name, g.name)
 
 
+# thread-block shapes whose tables reach 2^12 and 2^13 buckets: with 100 KB
+# blocks a part holds up to 4096 keys, with 200 KB up to 8192, and the
+# signature probe is compiled once per table size (2^6 .. 2^13 buckets)
+BLOCK_SHAPES = {
+    "default": {},
+    "blocks_100k": dict(block_threads=512, block_smem_bytes=100 * 1024, item_neighbors=512),
+    "blocks_200k": dict(block_threads=1024, block_smem_bytes=200 * 1024, item_neighbors=1024),
+}
+
+
+@pytest.mark.parametrize("shape", sorted(BLOCK_SHAPES))
+def test_block_table_sizes(T, shape):
+    # K_2100: vertex i keeps the 2099 - i larger ids, so the thread-block tables
+    # run through every size from 2^6 buckets up to the shape's largest part
+    k = G.complete(2100)
+    g = G.rmat(14, 16, seed=17)
+    with T.Context(0, params=BLOCK_SHAPES[shape]) as c:
+        assert gpu_count(c, k) == math.comb(2100, 3)
+        assert gpu_count(c, g) == oracle.count(g)
+
+
 def _bucket_collision_graph(k, stride=1024):
     # u = 0 joined to k vertices whose ids are multiples of `stride`, which form
     # a clique: every key of N+(0) hashes to bucket 0 for any B <= stride.
