@@ -920,7 +920,10 @@ __device__ __forceinline__ uint32_t vc_range_oct(int s, int e, int no, int tab, 
 // FMA pipe (measured: thread-block workers 3 % faster on R-MAT 22 and 24).
 __device__ __forceinline__ unsigned lds_word(unsigned i, unsigned base) {
     unsigned v;
-    asm("{\n\t.reg .b32 a;\n\tmad.lo.u32 a, %1, 4, %2;\n\tld.shared.u32 %0, [a];\n\t}" : "=r"(v) : "r"(i), "r"(base));
+    // volatile: the read must stay after the barrier that publishes the words
+    asm volatile("{\n\t.reg .b32 a;\n\tmad.lo.u32 a, %1, 4, %2;\n\tld.shared.u32 %0, [a];\n\t}"
+                 : "=r"(v)
+                 : "r"(i), "r"(base));
     return v;
 }
 
