@@ -98,7 +98,9 @@ typedef struct {
  * 6 levels of them cached in shared memory): a warp worker's table has buckets
  * of 2 keys (one 8-byte load per probe), a thread-block worker's table buckets
  * of 4 keys (one 16-byte load). A key whose bucket is full goes to the next
- * bucket. */
+ * bucket. A thread-block table in which every key sits in its home bucket
+ * also keeps a 32-bit key signature per bucket; a probe reads the signature
+ * word and loads the bucket only when the key's signature bit is set. */
 typedef struct {
     int32_t warp_max_out_degree; /* d+ above this -> thread-block worker, <= 255 (paper: 100; default 128) */
     int32_t warp_area_ints;      /* shared-memory table area of one warp worker, ints (default 1152);
