@@ -58,3 +58,24 @@ def test_default_workload_is_rmat26_with_int64_offsets():
     assert w["name"] == "rmat-s26-ef16-seed3" and w["offset_bits"] == 64
     golden = json.load(open(os.path.join(ROOT, "tests", "golden", w["golden"])))
     assert golden["workload"] == w["name"] and golden["triangles"] > 2 ** 32
+
+
+def test_host_reservations_cover_the_workloads():
+    # the end-to-end host buffers are mapped before the graph exists, from each
+    # workload's bounds on n and nnz: the generated graphs must fit them
+    sys.path.insert(0, ROOT)
+    import bench
+    import graphgen as G
+    for key in ("rmat16", "rmat22", "rgg22"):
+        spec = bench.WORKLOADS[key]
+        g = G.workload(spec["graph"])
+        assert g.n == spec["n"], key
+        assert g.nnz <= spec["nnz_max"], key
+    spec = bench.WORKLOADS["rmat26"]  # 2 * edge factor * 2^scale entries at most
+    assert spec["n"] == 1 << 26 and spec["nnz_max"] >= 2 * 16 * (1 << 26)
+    # a reservation is whole 2 MiB pages of touched anonymous memory
+    ptr, nbytes = bench.HugePinned.reserve(3 << 20)
+    try:
+        assert nbytes == 4 << 20 and ptr
+    finally:
+        bench.HugePinned._c().munmap(ptr, nbytes)
